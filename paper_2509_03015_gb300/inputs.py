@@ -1,0 +1,149 @@
+"""Seeded synthetic inputs for the block-tridiagonal SPD solver.
+
+This module only *draws* problems; it holds none of the solver's arithmetic
+(no factorisation, no solve, no Schur complement).  Both the CUDA path's tests
+and benchmark and the CPU oracle's tests take their inputs from here.
+
+Layout of every problem (the operator of Eq. 1, Sec. 1):
+  A_diag : (N, n, n) float64, A_diag[i] = A_{i+1,i+1} in the paper's 1-based
+           numbering (row-major; the solver uses sym(A_diag[i])).
+  A_sub  : (N-1, n, n) float64, A_sub[i] = A_{i+2,i+1}, the block *below* the
+           diagonal; the block above it is its transpose.
+  B      : (N, n, d) float64, i.e. the (N*n) x d right-hand side, row-major.
+
+Generators:
+  kalman_btd     -- the Kalman-smoother normal equations of Sec. 4.2 (Eq. 6 and
+                    the block formulas after it), time-invariant F, H, Q, R.
+  mpc_batch_shapes -- (N_k, n_k) of the 512-instance uneven batch.
+  random_btd     -- per-block random SPD systems (every block distinct), used by
+                    the parity tests so that an indexing mistake cannot hide
+                    behind repeated blocks.
+  tridiag_121    -- n = 1, A = tridiag(-1, 2, -1), B = 1.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Named workloads.  Sizes follow the Kalman-smoother recipe: F = rho * Haar
+# orthogonal, H Gaussian / sqrt(n), Q = 0.1 I, R = 0.5 I, P0 = I.
+WORKLOADS = {
+    # small plain FP64 solve
+    "kalman-N64-n8-d1": dict(N=64, n=8, m=4, d=1, rho=0.95, seed=0),
+    # the fused persistent FP64 path (roofline and level-fusion benchmark)
+    "kalman-N16384-n64-d4": dict(N=16384, n=64, m=32, d=4, rho=0.95, seed=0),
+    # mixed precision with refinement, kappa(A) pushed towards 1e5
+    "kalman-N4096-n256-d16-rho0.99": dict(N=4096, n=256, m=128, d=16, rho=0.99, seed=0),
+    # differentiation (forward + adjoint backward); W drawn after B
+    "kalman-N2048-n32-d8-grad": dict(N=2048, n=32, m=16, d=8, rho=0.95, seed=0),
+}
+
+# The uneven batch: 512 condensed-MPC-like systems.
+MPC_BATCH = dict(K=512, N_lo=32, N_hi=2048, n_choices=(12, 24, 48), d=1, rho=0.95, seed=0)
+
+
+def haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Haar-distributed orthogonal matrix: QR of a standard Gaussian with the
+    sign of diag(R) folded into Q (Mezzadri 2007)."""
+    G = rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s[None, :]
+
+
+def kalman_blocks(n: int, m: int, rho: float, rng: np.random.Generator):
+    """The distinct blocks of the time-invariant Kalman-smoother Hessian.
+
+    Sec. 4.2: A_kk = Q^-1 + G_{k+1}^T Q^-1 G_{k+1} + H^T R^-1 H,
+    A_{k+1,k} = -Q^-1 G_{k+1}, G_{N+1} = 0; the first block carries the prior
+    P0^-1 in place of Q^-1.  Returns (first, middle, last, only, sub) where
+    `only` is the single block of an N = 1 system.
+    """
+    F = rho * haar_orthogonal(rng, n)
+    H = rng.standard_normal((m, n)) / math.sqrt(n)
+    Qinv = 10.0 * np.eye(n)          # Q = 0.1 I
+    Rinv = 2.0 * np.eye(m)           # R = 0.5 I (m x m)
+    P0inv = np.eye(n)                # P0 = I
+    HtRH = H.T @ Rinv @ H
+    FtQF = F.T @ Qinv @ F
+    first = P0inv + HtRH + FtQF
+    middle = Qinv + HtRH + FtQF
+    last = Qinv + HtRH
+    only = P0inv + HtRH
+    sub = -(Qinv @ F)
+    return first, middle, last, only, sub
+
+
+def kalman_btd(N: int, n: int, m: int, d: int, rho: float, seed: int, with_W: bool = False):
+    """One Kalman-smoother system.  Draw order: the Haar Gaussian, then H,
+    then B, then (optionally) W, all from numpy.random.default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    first, middle, last, only, sub = kalman_blocks(n, m, rho, rng)
+    A_diag = np.empty((N, n, n), dtype=np.float64)
+    if N == 1:
+        A_diag[0] = only
+    else:
+        A_diag[:] = middle
+        A_diag[0] = first
+        A_diag[N - 1] = last
+    A_sub = np.empty((max(N - 1, 0), n, n), dtype=np.float64)
+    A_sub[:] = sub
+    B = rng.standard_normal((N * n, d)).reshape(N, n, d)
+    out = dict(A_diag=A_diag, A_sub=A_sub, B=np.ascontiguousarray(B))
+    if with_W:
+        out["W"] = rng.standard_normal((N * n, d)).reshape(N, n, d)
+    return out
+
+
+def workload(name: str, with_W: bool = False):
+    cfg = WORKLOADS[name]
+    return kalman_btd(cfg["N"], cfg["n"], cfg["m"], cfg["d"], cfg["rho"], cfg["seed"], with_W=with_W)
+
+
+def mpc_batch_shapes(K: int = 512, N_lo: int = 32, N_hi: int = 2048, n_choices=(12, 24, 48), seed: int = 0):
+    """(N_k, n_k) for the uneven batch: a master default_rng(seed) draws
+    N_k = floor(exp(U(ln N_lo, ln N_hi))) and n_k uniformly from n_choices,
+    for k = 0..K-1 (N first, then n, per instance)."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    for _ in range(K):
+        Nk = int(math.floor(math.exp(rng.uniform(math.log(N_lo), math.log(N_hi)))))
+        nk = int(n_choices[int(rng.integers(0, len(n_choices)))])
+        shapes.append((max(Nk, 1), nk))
+    return shapes
+
+
+def mpc_batch(K: int = 512, d: int = 1, rho: float = 0.95, seed: int = 0, **kw):
+    """The batch: instance k is a Kalman system with seed k, m = n_k / 2."""
+    shapes = mpc_batch_shapes(K=K, seed=seed, **kw)
+    return [kalman_btd(Nk, nk, max(nk // 2, 1), d, rho, k) for k, (Nk, nk) in enumerate(shapes)]
+
+
+def random_btd(N: int, n: int, d: int, seed: int, coupling: float = 1.0):
+    """Per-block random SPD block-tridiagonal system.
+
+    A_sub[i] ~ coupling * Gaussian / sqrt(n); A_diag[i] = M M^T / n + s_i I with
+    s_i = ||A_{i,i-1}||_2 + ||A_{i,i+1}||_2 + 1, which makes A block diagonally
+    dominant in the 2-norm and hence SPD.  A_diag is returned slightly
+    non-symmetric on purpose (a skew part of size 1e-3) so that the sym(.)
+    reading of the diagonal blocks is exercised.
+    """
+    rng = np.random.default_rng(seed)
+    A_sub = coupling * rng.standard_normal((max(N - 1, 0), n, n)) / math.sqrt(n)
+    norms = np.array([np.linalg.norm(A_sub[i], 2) for i in range(N - 1)]) if N > 1 else np.zeros(0)
+    A_diag = np.empty((N, n, n))
+    for i in range(N):
+        M = rng.standard_normal((n, n))
+        s = 1.0 + (norms[i - 1] if i > 0 else 0.0) + (norms[i] if i < N - 1 else 0.0)
+        skew = rng.standard_normal((n, n)) * 1e-3
+        A_diag[i] = M @ M.T / n + s * np.eye(n) + (skew - skew.T)
+    B = rng.standard_normal((N, n, d))
+    return dict(A_diag=A_diag, A_sub=A_sub, B=B)
+
+
+def tridiag_121(N: int, d: int = 1):
+    """n = 1: A = tridiag(-1, 2, -1), B = all ones."""
+    return dict(A_diag=np.full((N, 1, 1), 2.0), A_sub=np.full((max(N - 1, 0), 1, 1), -1.0),
+                B=np.ones((N, 1, d)))
