@@ -1,0 +1,153 @@
+/*
+ * bdss.h -- C ABI of the GB300 (sm_103a) block-tridiagonal SPD solver.
+ *
+ * Solves A X = B where A is symmetric positive definite and block-tridiagonal
+ * (Eq. 1, Sec. 1): N diagonal blocks A_{i,i} of size n x n, N-1 sub-diagonal
+ * blocks A_{i+1,i} (the block above the diagonal is A_{i+1,i}^T), and X, B of
+ * size (N n) x d.  The method is the recursive Schur-complement reduction of
+ * Sec. 3 (Eq. 2-5, Algorithms 1-7) with interior segments of length one,
+ * i.e. odd-even block cyclic reduction: at every level the odd positions are
+ * eliminated and the even positions are the separators of the next level.
+ *
+ * Data layout (all row-major, 0-based block indices, device memory unless a
+ * parameter says "host"):
+ *   A_diag : N x n x n doubles, A_diag[i] = A_{i,i}.  The operator reads
+ *            sym(A_{i,i}) = (A_{i,i} + A_{i,i}^T) / 2.
+ *   A_sub  : (N-1) x n x n doubles, A_sub[i] = A_{i+1,i}.  May be NULL iff N == 1.
+ *   B, X   : N x n x d doubles, element (i, r, k) at ((i n + r) d + k).
+ * Every device pointer must be 16-byte aligned.
+ *
+ * Ownership.  The caller owns every input and output buffer; the library never
+ * frees them.  A handle owns its workspace (factors of every level, the
+ * level coupling blocks, a status word).  In the mixed-precision modes the
+ * handle also remembers the A_diag / A_sub pointers given to bdss_factor and
+ * reads them again in bdss_solve to form the FP64 residual: the caller must
+ * keep them valid and unmodified until the next bdss_factor or bdss_destroy.
+ *
+ * Streams.  All work is enqueued on the CUDA stream given to bdss_create
+ * (NULL = legacy default stream).  Each call that launches work synchronises
+ * that stream before it returns, in order to read the device status word.
+ *
+ * Errors.  Functions return a bdss_status; they never abort or print.
+ * Arguments are checked on the host before anything is launched.
+ * Device-side failures (a non-positive or non-finite Cholesky pivot; a grid
+ * barrier wait that exceeded its time limit) are reported through the status
+ * word and leave the device usable.
+ */
+#ifndef BDSS_H
+#define BDSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bdss_ctx *bdss_handle;
+
+typedef enum {
+  BDSS_OK = 0,
+  BDSS_ERR_INVALID_ARG = 1,     /* bad size, NULL or misaligned pointer, d > d_max, ... */
+  BDSS_ERR_NOT_SPD = 2,         /* a Cholesky pivot was <= 0 or not finite; see bdss_info */
+  BDSS_ERR_NOT_FACTORED = 3,    /* bdss_solve / bdss_logdet before a successful bdss_factor */
+  BDSS_ERR_ALLOC = 4,           /* device or pinned-host allocation failed */
+  BDSS_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+  BDSS_ERR_TIMEOUT = 6,         /* a device-side wait exceeded its time limit */
+  BDSS_ERR_NO_CONVERGENCE = 7,  /* mixed precision: refinement did not reach the target */
+  BDSS_ERR_UNSUPPORTED = 8      /* a size or mode this build does not implement */
+} bdss_status;
+
+typedef enum {
+  BDSS_FP64 = 0,     /* every step in FP64 (DFMA) */
+  BDSS_FP32_IR = 1,  /* factor/solve in FP32, FP64 residual + iterative refinement */
+  BDSS_TF32_IR = 2   /* as FP32_IR, Schur-update products on TF32 tensor cores */
+} bdss_precision;
+
+typedef struct {
+  int64_t level;        /* NOT_SPD: reduction level of the failing pivot (-1: none) */
+  int64_t block;        /* NOT_SPD: original 0-based block index of that pivot */
+  int32_t iters;        /* mixed precision: refinement steps taken (0 in FP64) */
+  int32_t reserved;
+  double backward_err;  /* mixed precision: ||B-AX||_inf / (||A||_inf ||X||_inf) of
+                           the returned X, FP64 residual; -1 when not computed */
+} bdss_info;
+
+/* Options for bdss_set_option. */
+typedef enum {
+  BDSS_OPT_TIMEOUT_MS = 0,      /* limit of every device-side wait (default 10000) */
+  BDSS_OPT_PERSISTENT = 1,      /* 1 (default): one persistent launch with grid barriers
+                                   per factor / solve; 0: one launch per level and phase
+                                   (the per-level structure of Algorithms 4 and 7) */
+  BDSS_OPT_MAX_REFINE = 2,      /* mixed precision: refinement step limit (default 10) */
+  BDSS_OPT_TARGET_BERR_E18 = 3, /* mixed precision: target backward error x 1e18
+                                   (default 10000 = 1e-14) */
+  BDSS_OPT_DEBUG_SKIP_ARRIVE = 4 /* test hook: CTA 0 skips its arrival at the given
+                                   grid barrier (1-based; 0 = off) so that the waits
+                                   of the others run out and BDSS_ERR_TIMEOUT results */
+} bdss_option;
+
+/*
+ * Create a solver for systems with N >= 1 blocks of size 1 <= n <= 64 and up
+ * to d_max >= 1 right-hand-side columns, allocating all device workspace
+ * (the "Init" phase of the evaluation in Sec. 4.2).  `cuda_stream` is a
+ * cudaStream_t (NULL = default stream).  On success *h is a new handle.
+ */
+bdss_status bdss_create(bdss_handle *h, int64_t N, int32_t n, int32_t d_max,
+                        bdss_precision prec, void *cuda_stream);
+
+/* Set an option (see bdss_option).  Returns BDSS_ERR_INVALID_ARG for an
+ * unknown key or a value out of range. */
+bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value);
+
+/*
+ * Factor A (Algorithm 4, all levels): at level l, for every eliminated block
+ * j: L_j = chol(A_jj) (Algorithm 1, potrf), W_L = L_j^{-1} A_{j,j-1} and
+ * W_R = L_j^{-1} A_{j+1,j}^T (Sec. 3.3 stage 2, trsm); for every separator s:
+ * S_ss = A_ss - W_R(s-1)^T W_R(s-1) - W_L(s+1)^T W_L(s+1) and
+ * S_{s+2,s} = -W_R(s+1)^T W_L(s+1) (Algorithm 3 and Eq. 5, gemm + Assemble);
+ * then the single remaining block is factored in FP64.  A_diag and A_sub are
+ * not modified.  On BDSS_ERR_NOT_SPD, info->level / info->block name the
+ * failing pivot (if info != NULL).
+ */
+bdss_status bdss_factor(bdss_handle h, const double *A_diag, const double *A_sub,
+                        bdss_info *info);
+
+/*
+ * Solve with the stored factors (Algorithm 7): upward RHS reduction
+ * y_j = L_j^{-1} b_j, b_s -= W^T y (Algorithm 5), the top solve, then the
+ * downward back-substitution x_j = L_j^{-T}(y_j - W_L x_{j-1} - W_R x_{j+1})
+ * (Algorithms 6 and 2).  1 <= d <= d_max.  X may equal B (in place); otherwise
+ * B is not modified.  In the mixed modes this runs the refinement loop and
+ * fills info->iters and info->backward_err.
+ */
+bdss_status bdss_solve(bdss_handle h, const double *B, double *X, int32_t d, bdss_info *info);
+
+/* bdss_factor followed by bdss_solve, with the upward RHS reduction riding
+ * on the factor's levels (one fewer pass over the levels). */
+bdss_status bdss_factor_solve(bdss_handle h, const double *A_diag, const double *A_sub,
+                              const double *B, double *X, int32_t d, bdss_info *info);
+
+/* log det A = sum over every eliminated block and the top block of
+ * 2 sum_k log (L)_kk (det of the permuted matrix = det A_uu det S, Eq. 5),
+ * from the stored factors.  `out` is a host pointer. */
+bdss_status bdss_logdet(bdss_handle h, double *out);
+
+/* Number of grid barriers / kernel launches the last factor or solve issued
+ * (host pointers, either may be NULL). */
+bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
+
+/* Description of the last CUDA runtime error that made a bdss_* call on this
+ * host thread return BDSS_ERR_CUDA ("no error" if none).  Never NULL. */
+const char *bdss_last_cuda_error(void);
+
+/* Release the handle and its workspace.  NULL-safe. */
+bdss_status bdss_destroy(bdss_handle h);
+
+/* Static description of a status code (never NULL). */
+const char *bdss_status_string(bdss_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDSS_H */

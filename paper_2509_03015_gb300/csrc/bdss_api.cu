@@ -1,0 +1,457 @@
+// C ABI of the solver (include/bdss.h): handle and workspace ownership,
+// argument checks, the level plan, launches and the mixed-precision
+// refinement loop.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/bdss.h"
+#include "bdss_launch.h"
+
+using namespace bdss;
+
+struct bdss_ctx {
+  int64_t N = 0;
+  int n = 0;
+  int d_max = 0;
+  bdss_precision prec = BDSS_FP64;
+  cudaStream_t stream = nullptr;
+  Plan plan{};
+  int sms = 0;
+  int bps = 0;          // resident CTAs per SM of the persistent kernel
+  size_t smem = 0;      // dynamic shared memory per CTA
+  // workspace
+  void *Ld = nullptr;   // N n n  (T)
+  void *Wb = nullptr;   // coupling slots (T)
+  double *Ltop = nullptr;
+  float *Y32 = nullptr;  // mixed: working RHS / correction (N n d_max)
+  float *R32 = nullptr;  // mixed: FP32 residual (N n d_max)
+  double *partial = nullptr;  // log-det partial sums
+  DevStatus *dst = nullptr;
+  DevStatus *hst = nullptr;   // pinned
+  // state
+  bool factored = false;
+  const double *A_diag = nullptr;  // remembered for the FP64 residual (mixed)
+  const double *A_sub = nullptr;
+  double normA = 0.0;
+  // options
+  long long timeout_ns = 10000000000LL;
+  int persistent = 1;
+  int max_refine = 10;
+  double target = 1e-14;
+  int skip_barrier = 0;
+  // stats of the last call
+  int64_t launches = 0;
+  int64_t barriers = 0;
+};
+
+static constexpr int kLogdetGrid = 256;
+
+// Last CUDA runtime error met by a bdss_* call on this host thread.
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+static bdss_status cuda_fail(cudaError_t e) {
+  g_last_cuda_error = e;
+  return BDSS_ERR_CUDA;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static bool is_mixed(const bdss_ctx *h) { return h->prec != BDSS_FP64; }
+
+static void make_plan(Plan &p, int64_t N, int n) {
+  memset(&p, 0, sizeof(p));
+  p.N = N;
+  p.n = n;
+  p.Nl[0] = N;
+  p.off[0] = 0;
+  int l = 0;
+  while (p.Nl[l] > 1) {
+    p.Nl[l + 1] = (p.Nl[l] + 1) / 2;
+    p.off[l + 1] = p.off[l] + (p.Nl[l] - 1);
+    ++l;
+  }
+  p.L = l;
+}
+
+static int grid_for(const bdss_ctx *h, long long items) {
+  long long g = (long long)h->bps * h->sms;
+  if (items < g) g = items;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Read the device status word (synchronises the handle's stream).
+static bdss_status finish(bdss_ctx *h, bdss_info *info) {
+  cudaError_t e = cudaMemcpyAsync(h->hst, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int st = h->hst->status;
+  if (info && st == BDSS_ERR_NOT_SPD) {
+    info->level = h->hst->level;
+    info->block = h->hst->block;
+  }
+  return (bdss_status)st;
+}
+
+static cudaError_t reset_status(bdss_ctx *h) {
+  return cudaMemsetAsync(h->dst, 0, sizeof(DevStatus), h->stream);
+}
+
+template <typename T>
+static Args<T> base_args(bdss_ctx *h) {
+  Args<T> a;
+  memset(&a, 0, sizeof(a));
+  a.p = h->plan;
+  a.Ld = (T *)h->Ld;
+  a.Wb = (T *)h->Wb;
+  a.Ltop = h->Ltop;
+  a.st = h->dst;
+  a.timeout_ns = h->timeout_ns;
+  a.skip_barrier = h->skip_barrier;
+  return a;
+}
+
+// One factor and/or RHS pass over all levels, persistent or per level.
+template <typename T>
+static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool rhs) {
+  const Plan &p = h->plan;
+  if (h->persistent) {
+    const int grid = grid_for(h, (p.N + 1) / 2);
+    h->launches += 1;
+    int bars = 2 * p.L;
+    if (rhs && p.L > 0) bars += 1 + (p.L - 1);
+    h->barriers += bars;
+    return launch_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid, h->smem, h->stream);
+  }
+  Args<T> b = a;
+  if (!rhs) b.d = 0;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < p.L && e == cudaSuccess; ++l) {
+    const long long nElim = p.Nl[l] / 2, nSep = (p.Nl[l] + 1) / 2;
+    e = launch_phaseA<T>(b, l, factor ? 1 : 0, grid_for(h, nElim), h->smem, h->stream);
+    if (e == cudaSuccess) e = launch_phaseB<T>(b, l, factor ? 1 : 0, grid_for(h, nSep), h->smem, h->stream);
+    h->launches += 2;
+  }
+  if (e == cudaSuccess) e = launch_top<T>(b, factor ? 1 : 0, h->smem, h->stream);
+  h->launches += 1;
+  if (rhs)
+    for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
+      e = launch_phaseC<T>(b, l, grid_for(h, p.Nl[l] / 2), h->smem, h->stream);
+      h->launches += 1;
+    }
+  return e;
+}
+
+extern "C" {
+
+const char *bdss_status_string(bdss_status s) {
+  switch (s) {
+    case BDSS_OK: return "ok";
+    case BDSS_ERR_INVALID_ARG: return "invalid argument";
+    case BDSS_ERR_NOT_SPD: return "matrix not SPD (non-positive or non-finite pivot)";
+    case BDSS_ERR_NOT_FACTORED: return "not factored";
+    case BDSS_ERR_ALLOC: return "allocation failed";
+    case BDSS_ERR_CUDA: return "CUDA runtime error";
+    case BDSS_ERR_TIMEOUT: return "device wait timed out";
+    case BDSS_ERR_NO_CONVERGENCE: return "refinement did not converge";
+    case BDSS_ERR_UNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown status";
+}
+
+bdss_status bdss_destroy(bdss_handle h) {
+  if (!h) return BDSS_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->Ld);
+  cudaFree(h->Wb);
+  cudaFree(h->Ltop);
+  cudaFree(h->Y32);
+  cudaFree(h->R32);
+  cudaFree(h->partial);
+  cudaFree(h->dst);
+  if (h->hst) cudaFreeHost(h->hst);
+  delete h;
+  return BDSS_OK;
+}
+
+bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, bdss_precision prec,
+                        void *cuda_stream) {
+  if (!out) return BDSS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (N < 1 || n < 1 || d_max < 1 || d_max > 64) return BDSS_ERR_INVALID_ARG;
+  if (prec != BDSS_FP64 && prec != BDSS_FP32_IR && prec != BDSS_TF32_IR) return BDSS_ERR_INVALID_ARG;
+  if (n > kMaxN) return BDSS_ERR_UNSUPPORTED;
+  if (N > ((int64_t)1 << (kMaxLevels - 2))) return BDSS_ERR_UNSUPPORTED;
+  bdss_ctx *h = new (std::nothrow) bdss_ctx();
+  if (!h) return BDSS_ERR_ALLOC;
+  h->N = N;
+  h->n = n;
+  h->d_max = d_max;
+  h->prec = prec;
+  h->stream = (cudaStream_t)cuda_stream;
+  make_plan(h->plan, N, n);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  int smem_optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) { bdss_destroy(h); return cuda_fail(e); }
+  const size_t esz = is_mixed(h) ? sizeof(float) : sizeof(double);
+  const size_t need = is_mixed(h) ? smem_bytes<float>(n, d_max) : smem_bytes<double>(n, d_max);
+  if (need > (size_t)smem_optin) { bdss_destroy(h); return BDSS_ERR_UNSUPPORTED; }
+  e = is_mixed(h) ? configure<float>(n, d_max, &h->smem, &h->bps) : configure<double>(n, d_max, &h->smem, &h->bps);
+  if (e != cudaSuccess || h->bps < 1) { bdss_destroy(h); return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration); }
+  const size_t nn = (size_t)n * n;
+  const size_t slots = (size_t)(h->plan.off[h->plan.L] > 0 ? h->plan.off[h->plan.L] : 1);
+  bool ok = cudaMalloc(&h->Ld, (size_t)N * nn * esz) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->Wb, slots * nn * esz) == cudaSuccess;
+  ok = ok && cudaMalloc((void **)&h->Ltop, nn * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void **)&h->partial, kLogdetGrid * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void **)&h->dst, sizeof(DevStatus)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void **)&h->hst, sizeof(DevStatus)) == cudaSuccess;
+  if (ok && is_mixed(h)) {
+    const size_t nd = (size_t)N * n * d_max;
+    ok = cudaMalloc((void **)&h->Y32, nd * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->R32, nd * sizeof(float)) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();  // clear the allocation error
+    bdss_destroy(h);
+    return BDSS_ERR_ALLOC;
+  }
+  memset(h->hst, 0, sizeof(DevStatus));
+  *out = h;
+  return BDSS_OK;
+}
+
+bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  switch (key) {
+    case BDSS_OPT_TIMEOUT_MS:
+      if (value < 1 || value > 600000) return BDSS_ERR_INVALID_ARG;
+      h->timeout_ns = value * 1000000LL;
+      return BDSS_OK;
+    case BDSS_OPT_PERSISTENT:
+      if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
+      h->persistent = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_MAX_REFINE:
+      if (value < 0 || value > 100) return BDSS_ERR_INVALID_ARG;
+      h->max_refine = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_TARGET_BERR_E18:
+      if (value < 1) return BDSS_ERR_INVALID_ARG;
+      h->target = (double)value * 1e-18;
+      return BDSS_OK;
+    case BDSS_OPT_DEBUG_SKIP_ARRIVE:
+      if (value < 0) return BDSS_ERR_INVALID_ARG;
+      h->skip_barrier = (int)value;
+      return BDSS_OK;
+  }
+  return BDSS_ERR_INVALID_ARG;
+}
+
+static bdss_status check_factor_args(bdss_ctx *h, const double *A_diag, const double *A_sub) {
+  if (!A_diag || !aligned16(A_diag)) return BDSS_ERR_INVALID_ARG;
+  if (h->N > 1 && (!A_sub || !aligned16(A_sub))) return BDSS_ERR_INVALID_ARG;
+  return BDSS_OK;
+}
+
+static bdss_status check_solve_args(bdss_ctx *h, const double *B, double *X, int d) {
+  if (!B || !X || !aligned16(B) || !aligned16(X)) return BDSS_ERR_INVALID_ARG;
+  if (d < 1 || d > h->d_max) return BDSS_ERR_INVALID_ARG;
+  return BDSS_OK;
+}
+
+static void info_init(bdss_info *info) {
+  if (!info) return;
+  info->level = -1;
+  info->block = -1;
+  info->iters = 0;
+  info->reserved = 0;
+  info->backward_err = -1.0;
+}
+
+// Factor (and, if B != NULL, the first solve) -- both precisions.
+static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *A_sub, const double *B, double *X,
+                               int d, bdss_info *info) {
+  h->factored = false;
+  h->launches = 0;
+  h->barriers = 0;
+  const bool rhs = (B != nullptr);
+  cudaError_t e = reset_status(h);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!is_mixed(h)) {
+    Args<double> a = base_args<double>(h);
+    a.A_diag = A_diag;
+    a.A_sub = A_sub;
+    if (rhs) {
+      a.d = d;
+      a.B64 = B;
+      a.Y = X;
+    }
+    e = run_levels<double>(h, a, true, rhs);
+  } else {
+    Args<float> a = base_args<float>(h);
+    a.A_diag = A_diag;
+    a.A_sub = A_sub;
+    if (rhs) {
+      a.d = d;
+      a.B64 = B;
+      a.Y = h->Y32;
+      a.X64 = X;
+      a.x_accumulate = 0;
+    }
+    e = run_levels<float>(h, a, true, rhs);
+    if (e == cudaSuccess) {
+      e = launch_norm_A(h->N, h->n, A_diag, A_sub, h->dst, grid_for(h, h->N), h->stream);
+      h->launches += 1;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  bdss_status st = finish(h, info);
+  if (st != BDSS_OK) return st;
+  if (is_mixed(h)) {
+    uint64_t bits = h->hst->nrm[2];
+    memcpy(&h->normA, &bits, sizeof(double));
+  }
+  h->A_diag = A_diag;
+  h->A_sub = A_sub;
+  h->factored = true;
+  return BDSS_OK;
+}
+
+// Mixed precision: X already holds the FP32 solve; refine with FP64 residuals.
+static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_info *info) {
+  double prev = INFINITY;
+  int iters = 0;
+  bdss_status result = BDSS_ERR_NO_CONVERGENCE;
+  double berr = -1.0;
+  for (int it = 0;; ++it) {
+    cudaError_t e = reset_status(h);
+    if (e == cudaSuccess)
+      e = launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, grid_for(h, h->N) * 2,
+                          h->stream);
+    h->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(e);
+    bdss_status st = finish(h, nullptr);
+    if (st != BDSS_OK) return st;
+    double rn, xn;
+    uint64_t b0 = h->hst->nrm[0], b1 = h->hst->nrm[1];
+    memcpy(&rn, &b0, sizeof(double));
+    memcpy(&xn, &b1, sizeof(double));
+    const double den = h->normA * xn;
+    berr = den > 0 ? rn / den : (rn == 0 ? 0.0 : INFINITY);
+    if (berr <= h->target) { result = BDSS_OK; break; }
+    if (it > 0 && !(berr < 0.5 * prev)) break;   // stagnation
+    if (it >= h->max_refine) break;
+    prev = berr;
+    // correction: solve A dX = r in FP32, X += dX (FP64), fused in the downward pass
+    e = reset_status(h);
+    Args<float> a = base_args<float>(h);
+    a.d = d;
+    a.Bt = h->R32;
+    a.Y = h->Y32;
+    a.X64 = X;
+    a.x_accumulate = 1;
+    if (e == cudaSuccess) e = run_levels<float>(h, a, false, true);
+    if (e != cudaSuccess) return cuda_fail(e);
+    st = finish(h, nullptr);
+    if (st != BDSS_OK) return st;
+    ++iters;
+  }
+  if (info) {
+    info->iters = iters;
+    info->backward_err = berr;
+  }
+  return result;
+}
+
+bdss_status bdss_factor(bdss_handle h, const double *A_diag, const double *A_sub, bdss_info *info) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  info_init(info);
+  bdss_status st = check_factor_args(h, A_diag, A_sub);
+  if (st != BDSS_OK) return st;
+  return factor_impl(h, A_diag, A_sub, nullptr, nullptr, 0, info);
+}
+
+bdss_status bdss_solve(bdss_handle h, const double *B, double *X, int32_t d, bdss_info *info) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  info_init(info);
+  bdss_status st = check_solve_args(h, B, X, d);
+  if (st != BDSS_OK) return st;
+  if (!h->factored) return BDSS_ERR_NOT_FACTORED;
+  h->launches = 0;
+  h->barriers = 0;
+  cudaError_t e = reset_status(h);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!is_mixed(h)) {
+    Args<double> a = base_args<double>(h);
+    a.d = d;
+    a.B64 = B;
+    a.Y = X;
+    e = run_levels<double>(h, a, false, true);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return finish(h, info);
+  }
+  if (X == B) return BDSS_ERR_INVALID_ARG;  // the residual needs B after X is written
+  Args<float> a = base_args<float>(h);
+  a.d = d;
+  a.B64 = B;
+  a.Y = h->Y32;
+  a.X64 = X;
+  a.x_accumulate = 0;
+  e = run_levels<float>(h, a, false, true);
+  if (e != cudaSuccess) return cuda_fail(e);
+  st = finish(h, info);
+  if (st != BDSS_OK) return st;
+  return refine(h, B, X, d, info);
+}
+
+bdss_status bdss_factor_solve(bdss_handle h, const double *A_diag, const double *A_sub, const double *B, double *X,
+                              int32_t d, bdss_info *info) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  info_init(info);
+  bdss_status st = check_factor_args(h, A_diag, A_sub);
+  if (st == BDSS_OK) st = check_solve_args(h, B, X, d);
+  if (st != BDSS_OK) return st;
+  if (is_mixed(h) && X == B) return BDSS_ERR_INVALID_ARG;
+  st = factor_impl(h, A_diag, A_sub, B, X, d, info);
+  if (st != BDSS_OK || !is_mixed(h)) return st;
+  return refine(h, B, X, d, info);
+}
+
+bdss_status bdss_logdet(bdss_handle h, double *out) {
+  if (!h || !out) return BDSS_ERR_INVALID_ARG;
+  if (!h->factored) return BDSS_ERR_NOT_FACTORED;
+  const long long total = h->N * h->n;
+  int grid = (int)((total + kThreads - 1) / kThreads);
+  if (grid > kLogdetGrid) grid = kLogdetGrid;
+  cudaError_t e = is_mixed(h)
+                      ? launch_logdet<float>(h->N, h->n, (const float *)h->Ld, h->Ltop, h->partial, grid, h->stream)
+                      : launch_logdet<double>(h->N, h->n, (const double *)h->Ld, h->Ltop, h->partial, grid, h->stream);
+  double part[kLogdetGrid];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part, h->partial, grid * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  double s = 0.0;
+  for (int i = 0; i < grid; ++i) s += part[i];
+  *out = s;
+  return BDSS_OK;
+}
+
+const char *bdss_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda_error); }
+
+bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  if (kernel_launches) *kernel_launches = h->launches;
+  if (grid_barriers) *grid_barriers = h->barriers;
+  return BDSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,541 @@
+// Device side of odd-even block cyclic reduction for SPD block-tridiagonal
+// systems (Sec. 3, Eq. 2-5, Algorithms 1-7, interior segments of length one).
+//
+// Level l holds N_l = ceil(N / 2^l) blocks; its position j is original block
+// j << l.  Odd positions are eliminated, even positions are the separators
+// that form level l+1.  Storage (T = double or float):
+//   Ld   : N x n x n.  Slot of original block i.  After factoring, the slot of
+//          every eliminated block holds its Cholesky factor L (lower
+//          triangle; the diagonal holds 1 / L_kk), and the slot of every
+//          separator holds its updated diagonal block (lower triangle) until
+//          it is eliminated.  Block 0 is the top block; its FP64 factor is in
+//          Ltop (same convention).
+//   Wb   : coupling slots, region l = [off_l, off_l + N_l - 1).  Slot k of
+//          region l couples level-l positions k and k+1.  Region 0 is written
+//          only (its couplings are the caller's A_sub); region l >= 1 first
+//          receives the new sub-diagonal S_{k+1,k} (row-major, like A_sub)
+//          from the separators of level l-1, which the eliminated block of
+//          level l that owns the slot then overwrites with its W^T:
+//            eliminated j: slot j-1 <- W_L^T = (L_j^{-1} A_{j,j-1})^T,
+//                          slot j   <- W_R^T = (L_j^{-1} A_{j+1,j}^T)^T.
+//   Y    : N x n x d right-hand side / solution in T.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bdss {
+
+constexpr int kMaxLevels = 48;
+constexpr int kThreads = 256;
+constexpr int kMaxN = 64;
+
+enum { kStOk = 0, kStNotSPD = 2, kStTimeout = 6 };
+
+struct DevStatus {
+  unsigned int bar_count;  // arrivals at the current grid barrier
+  unsigned int bar_gen;    // generation of the grid barrier
+  int status;              // 0 = ok, else a bdss_status code
+  int pad;
+  long long level;         // NOT_SPD: level and original block of the pivot
+  long long block;
+  unsigned long long nrm[4];  // residual kernel: bit patterns of max-norms (>= 0)
+};
+
+struct Plan {
+  long long N;
+  int n;
+  int L;                         // levels with eliminations; N_L == 1
+  long long Nl[kMaxLevels + 1];  // N_l
+  long long off[kMaxLevels + 1]; // first Wb slot of region l
+};
+
+template <typename T>
+struct Args {
+  Plan p;
+  const double *A_diag;  // caller's blocks (FP64), read at level 0
+  const double *A_sub;
+  T *Ld;
+  T *Wb;
+  double *Ltop;
+  int d;                 // right-hand-side columns in this call (0: none)
+  const double *B64;     // level-0 RHS source in FP64, or null
+  const T *Bt;           // level-0 RHS source in T, or null
+  T *Y;                  // working RHS / solution (N x n x d)
+  double *X64;           // FP64 output; null if Y already is the output
+  int x_accumulate;      // X64 += x instead of X64 = x
+  DevStatus *st;
+  long long timeout_ns;
+  int skip_barrier;      // test hook: 1-based barrier index CTA 0 skips
+};
+
+// Odd row stride of a staged n x n block (shared-memory bank spread).
+__host__ __device__ __forceinline__ int ldstride(int n) { return (n & 1) ? n : n + 1; }
+
+template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_status(DevStatus *st, int code, long long level, long long block) {
+  if (atomicCAS(&st->status, 0, code) == 0) {
+    st->level = level;
+    st->block = block;
+  }
+}
+
+// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
+// timeout_ns (or an iteration cap) the waiting CTA records BDSS_ERR_TIMEOUT
+// and returns false; any recorded error also makes it return false.  The
+// caller must return from the kernel when it gets false.
+static __device__ __noinline__ bool grid_barrier(DevStatus *st, long long timeout_ns, int index, int skip) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_relaxed_i32(&st->status) != 0) {
+      ok = 0;
+    } else {
+      const unsigned gen = ld_acquire_u32(&st->bar_gen);
+      const bool skip_me = (skip == index) && (blockIdx.x == 0);
+      bool released = false;
+      if (!skip_me) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&st->bar_count, 1u);
+        if (prev == gridDim.x - 1) {
+          atomicExch(&st->bar_count, 0u);
+          __threadfence();
+          atomicAdd(&st->bar_gen, 1u);
+          released = true;
+        }
+      }
+      if (!released) {
+        const long long t0 = global_ns();
+        const unsigned long long cap = 1000000ull + (unsigned long long)(timeout_ns / 16);
+        unsigned long long spins = 0;
+        while (ld_acquire_u32(&st->bar_gen) == gen) {
+          if (ld_relaxed_i32(&st->status) != 0) { ok = 0; break; }
+          ++spins;
+          if ((spins & 31) == 0 && (global_ns() - t0 > timeout_ns || spins > cap)) {
+            set_status(st, kStTimeout, -1, -1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Staging helpers (all threads of the CTA participate).
+// ---------------------------------------------------------------------------
+
+// s[i*ld + c] = sym(A)[i][c] for c <= i, from a caller FP64 block.
+template <typename T>
+__device__ void stage_sym_lower(T *s, int ld, const double *g, int n) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, c = e - i * n;
+    if (c <= i) s[i * ld + c] = T(0.5) * ((T)ldcg(g + i * n + c) + (T)ldcg(g + c * n + i));
+  }
+}
+// s[i*ld + c] = g[i][c] for c <= i (lower triangle of a workspace block).
+template <typename T, typename S>
+__device__ void stage_lower(T *s, int ld, const S *g, int n) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, c = e - i * n;
+    if (c <= i) s[i * ld + c] = (T)ldcg(g + e);
+  }
+}
+// s[i*ld + c] = g[i][c] (a full n x n block).
+template <typename T, typename S>
+__device__ void stage_rows(T *s, int ld, const S *g, int n) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, c = e - i * n;
+    s[i * ld + c] = (T)ldcg(g + e);
+  }
+}
+// s[c*ld + i] = g[i][c]: the columns of an n x m row-major block become rows.
+template <typename T, typename S>
+__device__ void stage_cols(T *s, int ld, const S *g, int n, int m) {
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+    const int i = e / m, c = e - i * m;
+    s[c * ld + i] = (T)ldcg(g + e);
+  }
+}
+
+// Cholesky-Crout of the staged lower triangle (Algorithm 1, potrf), in
+// place: row i is handled by thread i; two barriers per column.  On exit the
+// diagonal holds 1 / L_kk.  Returns the first failing column + 1, or 0.
+template <typename T>
+__device__ int chol_staged(T *s, int ld, int n, int *s_flag) {
+  const int i = threadIdx.x;
+  if (i == 0) *s_flag = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    T acc = T(0);
+    if (i >= k && i < n) {
+      acc = s[i * ld + k];
+      const T *ri = s + i * ld;
+      const T *rk = s + k * ld;
+      for (int p = 0; p < k; ++p) acc = fma(-ri[p], rk[p], acc);
+      if (i == k) {
+        const bool ok = (acc > T(0)) && isfinite(acc);
+        const T l = ok ? sqrt(acc) : T(1);
+        s[k * ld + k] = T(1) / l;
+        if (!ok && *s_flag == 0) *s_flag = k + 1;
+      }
+    }
+    __syncthreads();
+    if (i > k && i < n) s[i * ld + k] = acc * s[k * ld + k];
+    __syncthreads();
+  }
+  return *s_flag;
+}
+
+// Forward substitution L w = v for `nv` staged vectors (rows of V, stride
+// ld), one vector per thread; L staged with reciprocal diagonal.
+template <typename T>
+__device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    T *w = V + v * ld;
+    for (int r = 0; r < n; ++r) {
+      T acc = w[r];
+      const T *lr = sL + r * ld;
+      for (int p = 0; p < r; ++p) acc = fma(-lr[p], w[p], acc);
+      w[r] = acc * lr[r];
+    }
+  }
+}
+
+// Backward substitution L^T z = t for `nv` staged vectors.
+template <typename T>
+__device__ void trsv_bwd_rows(const T *sL, int ld, int n, T *V, int nv) {
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    T *w = V + v * ld;
+    for (int r = n - 1; r >= 0; --r) {
+      T acc = w[r];
+      for (int p = r + 1; p < n; ++p) acc = fma(-sL[p * ld + r], w[p], acc);
+      w[r] = acc * sL[r * ld + r];
+    }
+  }
+}
+
+// Map a lower-triangle linear index t to (a, b), 0 <= b <= a.
+__device__ __forceinline__ void tri_index(int t, int &a, int &b) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  while (r * (r + 1) / 2 > t) --r;
+  a = r;
+  b = t - r * (r + 1) / 2;
+}
+
+// Shared-memory words (in T) of each phase.
+__host__ __device__ inline size_t smem_phaseA(int n, int d) {
+  const int ld = ldstride(n);
+  return (size_t)n * ld + (size_t)(2 * n + d) * ld + 8;
+}
+__host__ __device__ inline size_t smem_phaseB(int n, int d) {
+  const int ld = ldstride(n);
+  return (size_t)3 * n * ld + (size_t)2 * d * ld + 8;
+}
+__host__ __device__ inline size_t smem_down(int n, int d) {
+  const int ld = ldstride(n);
+  return (size_t)n * ld + (size_t)3 * d * ld + 8;
+}
+__host__ __device__ inline size_t smem_top_bytes(int n, int d) {
+  const int ld = ldstride(n);
+  return ((size_t)n * ld + (size_t)d * ld + 8) * sizeof(double);
+}
+
+// ---------------------------------------------------------------------------
+// Phase A: eliminated position j (odd) of level l.
+//   factor:  L_j = chol(D_j); W_L^T, W_R^T via forward substitution (trsm);
+//   rhs:     y_j = L_j^{-1} b_j (Algorithm 5's interior solve, fused).
+// With factor == false only the RHS part runs, using the stored L_j.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *smem, int *s_flag) {
+  const int n = a.p.n, ld = ldstride(n), d = a.d;
+  const long long Nl = a.p.Nl[l];
+  const bool hasR = (j + 1 < Nl);
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n;
+  T *sL = smem;
+  T *sV = sL + n * ld;
+  const int nW = factor ? (hasR ? 2 * n : n) : 0;  // coupling vectors
+  T *sB = sV + (size_t)(factor ? 2 * n : 0) * ld;   // RHS vectors
+
+  if (factor) {
+    if (l == 0) stage_sym_lower(sL, ld, a.A_diag + orig * nn, n);
+    else stage_lower(sL, ld, a.Ld + orig * nn, n);
+    // couplings: E_l[j-1] = A_{j,j-1} (columns), E_l[j] = A_{j+1,j} (rows)
+    if (l == 0) {
+      stage_cols(sV, ld, a.A_sub + (size_t)(j - 1) * nn, n, n);
+      if (hasR) stage_rows(sV + (size_t)n * ld, ld, a.A_sub + (size_t)j * nn, n);
+    } else {
+      const T *E = a.Wb + (size_t)a.p.off[l] * nn;
+      stage_cols(sV, ld, E + (size_t)(j - 1) * nn, n, n);
+      if (hasR) stage_rows(sV + (size_t)n * ld, ld, E + (size_t)j * nn, n);
+    }
+  } else {
+    stage_lower(sL, ld, a.Ld + orig * nn, n);
+  }
+  if (d > 0) {
+    const size_t boff = (size_t)orig * n * d;
+    if (l == 0 && a.B64) stage_cols(sB, ld, a.B64 + boff, n, d);
+    else if (l == 0 && a.Bt) stage_cols(sB, ld, a.Bt + boff, n, d);
+    else stage_cols(sB, ld, a.Y + boff, n, d);
+  }
+  __syncthreads();
+  if (factor) {
+    const int bad = chol_staged(sL, ld, n, s_flag);
+    if (bad) {
+      if (threadIdx.x == 0) set_status(a.st, kStNotSPD, l, orig);
+      __syncthreads();
+      return false;
+    }
+    T *Lg = a.Ld + orig * nn;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      if (c <= r) Lg[e] = sL[r * ld + c];
+    }
+  }
+  // forward substitution on the staged coupling vectors and the RHS vectors
+  {
+    const int rhs0 = factor ? 2 * n : 0;  // first RHS row of sV
+    for (int v = threadIdx.x; v < nW + d; v += blockDim.x) {
+      T *w = sV + (size_t)(v < nW ? v : rhs0 + (v - nW)) * ld;
+      for (int r = 0; r < n; ++r) {
+        T acc = w[r];
+        const T *lr = sL + r * ld;
+        for (int p = 0; p < r; ++p) acc = fma(-lr[p], w[p], acc);
+        w[r] = acc * lr[r];
+      }
+    }
+  }
+  __syncthreads();
+  if (factor) {
+    T *W = a.Wb + (size_t)a.p.off[l] * nn;
+    T *WL = W + (size_t)(j - 1) * nn;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int c = e / n, i = e - c * n;
+      WL[e] = sV[c * ld + i];
+    }
+    if (hasR) {
+      T *WR = W + (size_t)j * nn;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int c = e / n, i = e - c * n;
+        WR[e] = sV[(n + c) * ld + i];
+      }
+    }
+  }
+  if (d > 0) {
+    T *Yj = a.Y + (size_t)orig * n * d;
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int i = e / d, c = e - i * d;
+      Yj[e] = sB[c * ld + i];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Phase B: separator position s = 2k of level l (Algorithm 3 + Assemble,
+// Algorithm 5's separator update):
+//   S_ss      = D_s - W_R(s-1)^T W_R(s-1) - W_L(s+1)^T W_L(s+1)  (lower)
+//   S_{s+2,s} = -W_R(s+1)^T W_L(s+1)  -> region l+1, slot k
+//   b_s      -= W_R(s-1)^T y_{s-1} + W_L(s+1)^T y_{s+1}
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *smem) {
+  const int n = a.p.n, ld = ldstride(n), d = a.d;
+  const long long Nl = a.p.Nl[l];
+  const long long s = 2 * k;
+  const bool hasM = (s >= 2), hasP = (s + 1 < Nl), hasE = (s + 2 < Nl);
+  const long long orig = s << l;
+  const size_t nn = (size_t)n * n;
+  T *sW0 = smem;                      // W_R(s-1)^T
+  T *sW1 = sW0 + (size_t)n * ld;      // W_L(s+1)^T
+  T *sW2 = sW1 + (size_t)n * ld;      // W_R(s+1)^T
+  T *sY = sW2 + (size_t)n * ld;       // y_{s-1}, y_{s+1} as d vectors each
+  const T *W = a.Wb + (size_t)a.p.off[l] * nn;
+  if (hasM) stage_rows(sW0, ld, W + (size_t)(s - 1) * nn, n);
+  if (hasP) stage_rows(sW1, ld, W + (size_t)s * nn, n);
+  if (factor && hasE) stage_rows(sW2, ld, W + (size_t)(s + 1) * nn, n);
+  if (d > 0) {
+    if (hasM) stage_cols(sY, ld, a.Y + (size_t)((s - 1) << l) * n * d, n, d);
+    if (hasP) stage_cols(sY + (size_t)d * ld, ld, a.Y + (size_t)((s + 1) << l) * n * d, n, d);
+  }
+  __syncthreads();
+  if (factor) {
+    // diagonal update, lower triangle
+    T *Dg = a.Ld + (size_t)orig * nn;
+    const double *Ag = a.A_diag + (size_t)orig * nn;
+    const int ntri = n * (n + 1) / 2;
+    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+      int r, c;
+      tri_index(t, r, c);
+      T acc;
+      if (l == 0) acc = T(0.5) * ((T)ldcg(Ag + r * n + c) + (T)ldcg(Ag + c * n + r));
+      else acc = ldcg(Dg + r * n + c);
+      if (hasM) {
+        const T *wr = sW0 + r * ld, *wc = sW0 + c * ld;
+        for (int q = 0; q < n; ++q) acc = fma(-wr[q], wc[q], acc);
+      }
+      if (hasP) {
+        const T *wr = sW1 + r * ld, *wc = sW1 + c * ld;
+        for (int q = 0; q < n; ++q) acc = fma(-wr[q], wc[q], acc);
+      }
+      Dg[r * n + c] = acc;
+    }
+    if (hasE) {
+      T *En = a.Wb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        const T *wr = sW2 + r * ld, *wc = sW1 + c * ld;
+        T acc = T(0);
+        for (int q = 0; q < n; ++q) acc = fma(-wr[q], wc[q], acc);
+        En[e] = acc;
+      }
+    }
+  }
+  if (d > 0) {
+    const size_t boff = (size_t)orig * n * d;
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int r = e / d, c = e - r * d;
+      T acc;
+      if (l == 0 && a.B64) acc = (T)ldcg(a.B64 + boff + e);
+      else if (l == 0 && a.Bt) acc = ldcg(a.Bt + boff + e);
+      else acc = ldcg(a.Y + boff + e);
+      if (hasM) {
+        const T *wr = sW0 + r * ld, *y = sY + (size_t)c * ld;
+        for (int q = 0; q < n; ++q) acc = fma(-wr[q], y[q], acc);
+      }
+      if (hasP) {
+        const T *wr = sW1 + r * ld, *y = sY + (size_t)(d + c) * ld;
+        for (int q = 0; q < n; ++q) acc = fma(-wr[q], y[q], acc);
+      }
+      a.Y[boff + e] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Top block (the base case of Algorithms 4 and 7 with N_* = 1), always FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ bool top_block(const Args<T> &a, bool factor, double *smem, int *s_flag) {
+  const int n = a.p.n, ld = ldstride(n), d = a.d, L = a.p.L;
+  double *sL = smem;
+  double *sB = sL + (size_t)n * ld;
+  if (factor) {
+    if (L == 0) stage_sym_lower(sL, ld, a.A_diag, n);
+    else stage_lower(sL, ld, a.Ld, n);
+  } else {
+    stage_lower(sL, ld, a.Ltop, n);
+  }
+  if (d > 0) {
+    if (L == 0 && a.B64) stage_cols(sB, ld, a.B64, n, d);
+    else if (L == 0 && a.Bt) stage_cols(sB, ld, a.Bt, n, d);
+    else stage_cols(sB, ld, a.Y, n, d);
+  }
+  __syncthreads();
+  if (factor) {
+    if (chol_staged(sL, ld, n, s_flag)) {
+      if (threadIdx.x == 0) set_status(a.st, kStNotSPD, L, 0);
+      __syncthreads();
+      return false;
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      a.Ltop[e] = (c <= r) ? sL[r * ld + c] : 0.0;
+    }
+  }
+  if (d > 0) {
+    trsv_fwd_rows(sL, ld, n, sB, d);
+    __syncthreads();
+    trsv_bwd_rows(sL, ld, n, sB, d);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int i = e / d, c = e - i * d;
+      const double x = sB[c * ld + i];
+      a.Y[e] = (T)x;
+      if (a.X64) a.X64[e] = a.x_accumulate ? a.X64[e] + x : x;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Downward pass at level l, eliminated position j = 2m+1 (Algorithms 6, 2):
+//   x_j = L_j^{-T} (y_j - W_L x_{j-1} - W_R x_{j+1}).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void phaseC(const Args<T> &a, int l, long long j, T *smem) {
+  const int n = a.p.n, ld = ldstride(n), d = a.d;
+  const long long Nl = a.p.Nl[l];
+  const bool hasR = (j + 1 < Nl);
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  T *sL = smem;
+  T *sT = sL + (size_t)n * ld;          // t vectors (d)
+  T *sXm = sT + (size_t)d * ld;         // x_{j-1}
+  T *sXp = sXm + (size_t)d * ld;        // x_{j+1}
+  stage_lower(sL, ld, a.Ld + (size_t)orig * nn, n);
+  stage_cols(sXm, ld, a.Y + (size_t)((j - 1) << l) * nd, n, d);
+  if (hasR) stage_cols(sXp, ld, a.Y + (size_t)((j + 1) << l) * nd, n, d);
+  __syncthreads();
+  const T *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const T *WL = W + (size_t)(j - 1) * nn;   // W_L^T: WL[c][q] = W_L[q][c]
+  const T *WR = W + (size_t)j * nn;
+  const T *Yj = a.Y + (size_t)orig * nd;
+  // t[q][c] = y[q][c] - sum_a W_L[q][a] x_{j-1}[a][c] - sum_a W_R[q][a] x_{j+1}[a][c]
+  for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+    const int c = e / n, q = e - c * n;
+    T acc = ldcg(Yj + (size_t)q * d + c);
+    const T *xm = sXm + (size_t)c * ld;
+    for (int p = 0; p < n; ++p) acc = fma(-ldcg(WL + (size_t)p * n + q), xm[p], acc);
+    if (hasR) {
+      const T *xp = sXp + (size_t)c * ld;
+      for (int p = 0; p < n; ++p) acc = fma(-ldcg(WR + (size_t)p * n + q), xp[p], acc);
+    }
+    sT[c * ld + q] = acc;
+  }
+  __syncthreads();
+  trsv_bwd_rows(sL, ld, n, sT, d);
+  __syncthreads();
+  T *Yo = a.Y + (size_t)orig * nd;
+  for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+    const int i = e / d, c = e - i * d;
+    const T x = sT[c * ld + i];
+    Yo[e] = x;
+    if (a.X64) {
+      double *xo = a.X64 + (size_t)orig * nd + e;
+      *xo = a.x_accumulate ? *xo + (double)x : (double)x;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace bdss

@@ -1,0 +1,28 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "bdss_device.cuh"
+
+namespace bdss {
+
+template <typename T> size_t smem_bytes(int n, int d);
+template <typename T> cudaError_t configure(int n, int d, size_t *smem, int *blocks_per_sm);
+template <typename T>
+cudaError_t launch_persistent(const Args<T> &a, int factor, int rhs, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_phaseA(const Args<T> &a, int l, int factor, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_phaseB(const Args<T> &a, int l, int factor, int grid, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_top(const Args<T> &a, int factor, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_phaseC(const Args<T> &a, int l, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, double *partial, int grid,
+                          cudaStream_t s);
+cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
+                            const double *B, float *R32, DevStatus *st, int grid, cudaStream_t s);
+cudaError_t launch_norm_A(long long N, int n, const double *A_diag, const double *A_sub, DevStatus *st, int grid,
+                          cudaStream_t s);
+
+}  // namespace bdss

@@ -1,0 +1,84 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, exports
+every function include/bdss.h declares, the binding's signature table matches
+the header, and host-side argument checks reject bad input before anything
+touches the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bdss.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_03015_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bdss_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["bdss_create", "bdss_factor", "bdss_solve", "bdss_destroy", "bdss_factor_solve"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in bdss.h but not exported"
+
+
+def test_binding_covers_the_header():
+    from paper_2509_03015_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_no_cuda_symbols_leak_into_abi(lib):
+    # the exported C ABI carries no torch or C++ types
+    src = open(HEADER).read()
+    assert "torch" not in src and "std::" not in src and "at::" not in src
+
+
+def test_status_strings(lib):
+    for code in range(0, 9):
+        s = lib.bdss_status_string(code)
+        assert s and isinstance(s, bytes)
+    assert lib.bdss_status_string(0) == b"ok"
+
+
+def test_host_argument_checks(lib):
+    from paper_2509_03015_gb300 import _lib
+    h = ctypes.c_void_p()
+    # invalid sizes are rejected before any CUDA call
+    assert lib.bdss_create(ctypes.byref(h), 0, 8, 1, 0, None) == 1
+    assert lib.bdss_create(ctypes.byref(h), 10, 0, 1, 0, None) == 1
+    assert lib.bdss_create(ctypes.byref(h), 10, 8, 0, 0, None) == 1
+    assert lib.bdss_create(ctypes.byref(h), 10, 8, 65, 0, None) == 1
+    assert lib.bdss_create(ctypes.byref(h), 10, 8, 1, 7, None) == 1
+    assert lib.bdss_create(None, 10, 8, 1, 0, None) == 1
+    assert lib.bdss_create(ctypes.byref(h), 10, 65, 1, 0, None) == 8  # n > 64 not built yet
+    assert h.value is None
+    # NULL handles
+    assert lib.bdss_destroy(None) == 0
+    assert lib.bdss_set_option(None, 0, 1) == 1
+    info = _lib.bdss_info()
+    assert lib.bdss_factor(None, None, None, ctypes.byref(info)) == 1
+    assert lib.bdss_solve(None, None, None, 1, ctypes.byref(info)) == 1
+    out = ctypes.c_double()
+    assert lib.bdss_logdet(None, ctypes.byref(out)) == 1
+
+
+def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2509_03015_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load()

@@ -168,6 +168,19 @@ def test_logdet_kalman_small(oracle_mod):
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= 1e-15
 
 
+def test_logdet_long_sum_closed_form(oracle_mod):
+    """Block-diagonal A with N = 10^6 equal 1 x 1 blocks a = 4 (so L = 2
+    exactly): log det = N log 4.  The oracle's sum of 10^6 terms must stay
+    within a few ulps of the closed form (a plain running sum drifts by
+    ~1e-10 relative here)."""
+    N, a = 1_000_000, 4.0
+    A_diag = np.full((N, 1, 1), a)
+    A_sub = np.zeros((N - 1, 1, 1))
+    L, _ = oracle_mod.factor(A_diag, A_sub)
+    exact = N * math.log(a)
+    assert abs(oracle_mod.logdet(L) - exact) <= 8 * 2.0 ** -53 * exact
+
+
 def test_not_spd_detected(oracle_mod):
     s = inputs.random_btd(6, 4, 1, seed=3)
     s["A_diag"][4] -= 50.0 * np.eye(4)
