@@ -1,0 +1,338 @@
+"""Benchmark: factor + solve of the synthetic Kalman-smoother Hessian
+N = 16384 blocks, n = 64, d = 4 (FP64, fused persistent kernel), in
+systems/s, with the roofline of the kernel, the FP32 + FP64-refinement path,
+the per-level launch structure, an end-to-end figure through the C ABI with
+host buffers, the SM clocks seen, and the CPU oracle timed on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+replica of the system (independent problems: weak scaling, no collective on
+the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_03015_gb300 import accounting, inputs  # noqa: E402
+
+WORKLOAD = "kalman-N16384-n64-d4"
+METRIC = "systems/sec & % roofline, factor+solve; FP32+refine vs FP64 at backward err<=1e-14"
+PROFILE = os.path.join(ROOT, "profiles", "k_persistent_fp64_kalman-N16384-n64-d4.md")
+CSRC = os.path.join(ROOT, "paper_2509_03015_gb300", "csrc")
+L2_BYTES = 129 * 2 ** 20
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(N):
+    """DRAM bytes per launch from the committed ncu summary, scaled by the
+    blocks processed; None if the kernels changed since the capture."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m1 = re.search(r"csrc_sha256:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_block:\s*([0-9.eE+]+)", txt)
+    if not m1 or not m2 or m1.group(1) != csrc_digest():
+        return None
+    return float(m2.group(1)) * N
+
+
+def fp64_peak(sms, mhz):
+    """FP64 ALU peak: SMs x 2 DFMA/clk/SM x 2 flop x clock (GB300 FP64 rate)."""
+    return sms * 2 * 2 * mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.f.flush()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.f.name) as f:
+                for ln in f:
+                    p = [x.strip() for x in ln.split(",")]
+                    if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                        rows.append(p)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(float(r[1]) for r in rows), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def cpu_baseline(s, budget_s=10.0):
+    """The oracle (block-Thomas, sequential in N: one core) on a prefix of the
+    workload's blocks, sized for ~budget_s of CPU work; systems/s scaled by
+    N / prefix."""
+    import oracle
+    oracle.build()
+    N = s["A_diag"].shape[0]
+
+    def run(Ns):
+        t0 = time.perf_counter()
+        oracle.solve_system(s["A_diag"][:Ns], s["A_sub"][:Ns - 1], s["B"][:Ns])
+        return time.perf_counter() - t0
+    t = run(min(N, 64))
+    Ns = int(min(N, max(64, 64 * budget_s / max(t, 1e-9))))
+    t = run(Ns)
+    return {"value": (Ns / N) / t, "unit": "systems/s", "cores": 1, "kind": "oracle",
+            "sample": f"block-Thomas factor+solve of the first {Ns} of {N} blocks ({t:.2f} s), "
+                      f"scaled by {N}/{Ns}"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands on the host cores, same workload and metric;
+    each step a bounded prefix sample."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    s = inputs.workload(WORKLOAD)
+    N = s["A_diag"].shape[0]
+    Ns = 1024
+
+    def step():
+        oracle.solve_system(s["A_diag"][:Ns], s["A_sub"][:Ns - 1], s["B"][:Ns])
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps * (Ns / N) / el
+    sample = f"block-Thomas factor+solve of the first {Ns} of {N} blocks per step, scaled by {N}/{Ns}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps * (N / Ns),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "n": 64, "d": 4, "path": "CPU FP64 block-Thomas oracle"},
+        "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed / per-level / e2e legs")
+    ap.add_argument("--N", type=int, default=None,
+                    help="horizon override (same generator) for small profiling cases")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_03015_gb300 import Solver
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cfg = dict(inputs.WORKLOADS[WORKLOAD])
+    workload = WORKLOAD
+    if args.N is not None:
+        cfg["N"] = args.N
+        workload = f"kalman-N{args.N}-n64-d4"
+    N, n, d = cfg["N"], cfg["n"], cfg["d"]
+    s = inputs.kalman_btd(N, n, cfg["m"], d, cfg["rho"], cfg["seed"])
+    h_Ad = torch.from_numpy(s["A_diag"]).pin_memory()
+    h_As = torch.from_numpy(s["A_sub"]).pin_memory()
+    h_B = torch.from_numpy(s["B"]).pin_memory()
+    Ad, As, B = h_Ad.to(dev), h_As.to(dev), h_B.to(dev)
+    X = torch.empty_like(B)
+    in_bytes = (Ad.numel() + As.numel() + B.numel()) * 8
+
+    solver = Solver(N, n, d_max=d, precision="fp64", stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        solver.factor_solve(Ad, As, B, X)
+    launches_per_step, _bars = solver.launch_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            solver.factor_solve(Ad, As, B, X)
+            ev[k][1].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1))
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    value = world * args.steps / (elapsed_ms * 1e-3)
+    clocks = clk.summary()
+
+    tally = accounting.thomas_flops(N, n, d)
+    crf = accounting.cr_flops(N, n, d)
+    alg = tally["factor"] + tally["solve"]
+    exe = crf["factor"] + crf["solve"]
+    peak_mhz = clocks["sm_max_mhz"] or 2070.0
+    peak = fp64_peak(sm_count, peak_mhz)
+    achieved = alg / (launch_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "N": N, "n": n, "d": d, "m": cfg["m"], "rho": cfg["rho"],
+                   "seed": cfg["seed"], "path": "FP64 fused persistent factor+solve (one cooperative launch)",
+                   "l2": (f"inputs {in_bytes / 1e9:.2f} GB > 129 MB L2; no flush" if in_bytes > L2_BYTES
+                          else f"inputs {in_bytes / 1e6:.0f} MB fit in L2 (profiling case)"),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(N),
+                     "kernel": "bdss::k_persistent<double>", "flops_per_launch": alg,
+                     "flops_definition": "block-Thomas tally of the oracle (factor+solve)",
+                     "executed_flops_per_launch": exe, "executed_frac": exe / (launch_ms * 1e-3) / peak,
+                     "launch_ms": launch_ms,
+                     "peak_definition": f"{sm_count} SMs x 2 DFMA/clk x 2 flop x {peak_mhz:.0f} MHz; "
+                                        "a DFMA loop measured 1.194 TFLOP/s on this GPU"},
+        "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+
+    if not args.no_extras:
+        # FP32 factors + FP64 residual refinement on the same system
+        mixed = Solver(N, n, d_max=d, precision="fp32_ir", stream=stream)
+        X2 = torch.empty_like(B)
+        for _ in range(max(1, args.warmup)):
+            mixed.factor_solve(Ad, As, B, X2)
+        K2 = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K2):
+            mixed.factor_solve(Ad, As, B, X2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = max_over_ranks(e0.elapsed_time(e1)) / K2
+        info = mixed.last_info
+        out["fp32_ir"] = {"value": world * 1e3 / ms2, "unit": "systems/s", "ms_per_step": ms2,
+                          "refine_iters": info.iters, "backward_err": info.backward_err,
+                          "speedup_vs_fp64": (elapsed_ms / args.steps) / ms2}
+        mixed.close()
+        # the per-level launch structure (one launch per level and phase)
+        per = Solver(N, n, d_max=d, precision="fp64", stream=stream, persistent=False)
+        per.factor_solve(Ad, As, B, X2)
+        K3 = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K3):
+            per.factor_solve(Ad, As, B, X2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = max_over_ranks(e0.elapsed_time(e1)) / K3
+        out["per_level_launch"] = {"value": world * 1e3 / ms3, "unit": "systems/s", "ms_per_step": ms3,
+                                   "launches_per_step": per.launch_stats()[0]}
+        per.close()
+        # end to end through the C ABI with host buffers (pinned), copies timed
+        K4 = max(3, args.steps // 4)
+        h_X = torch.empty_like(h_B).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(K4):
+            Ad.copy_(h_Ad, non_blocking=True)
+            As.copy_(h_As, non_blocking=True)
+            B.copy_(h_B, non_blocking=True)
+            solver.factor_solve(Ad, As, B, X)
+            h_X.copy_(X, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms4 = max_over_ranks(e0.elapsed_time(e1)) / K4
+        out["e2e"] = {"value": world * 1e3 / ms4, "unit": "systems/s", "ms_per_step": ms4,
+                      "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": X.numel() * 8}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(s)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

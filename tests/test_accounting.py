@@ -1,0 +1,38 @@
+"""The benchmark's flop accounting against the oracle's tally and a direct
+count of the cyclic-reduction schedule."""
+import pytest
+
+from paper_2509_03015_gb300 import accounting
+
+
+@pytest.mark.parametrize("N,n,d", [(1, 1, 1), (2, 3, 1), (7, 5, 2), (64, 8, 1), (16384, 64, 4)])
+def test_thomas_matches_oracle_tally(oracle_mod, N, n, d):
+    t = oracle_mod.tally(N, n, d)
+    a = accounting.thomas_flops(N, n, d)
+    assert abs(a["factor"] - t["factor"]) <= 1e-12 * t["factor"]
+    assert abs(a["solve"] - t["solve"]) <= 1e-12 * t["solve"]
+
+
+def test_levels():
+    assert accounting.levels(1) == [1]
+    assert accounting.levels(2) == [2, 1]
+    assert accounting.levels(9) == [9, 5, 3, 2, 1]
+    assert accounting.levels(16384)[-2:] == [2, 1] and len(accounting.levels(16384)) == 15
+
+
+def test_cr_flops_small_cases():
+    n, d = 4, 2
+    c = accounting.chol_flops(n)
+    # N = 1: the top block only
+    assert accounting.cr_flops(1, n, d) == dict(factor=c, solve=2 * n * n * d)
+    # N = 2: block 1 eliminated with one coupling; separator 0 gets one update
+    f = accounting.cr_flops(2, n, d)
+    assert f["factor"] == c + n ** 3 + n * n * (n + 1) + c
+    assert f["solve"] == (n * n * d + 2 * n * n * d + n * n * d) + 2 * n * n * d + 2 * n * n * d
+
+
+def test_cr_over_thomas_ratio():
+    # cyclic reduction executes ~ (n^3/3 + 6 n^3) / (n^3/3 + 2 n^3) = 2.7x the
+    # block-Thomas factor flops for large N
+    r = accounting.cr_flops(16384, 64, 4)["factor"] / accounting.thomas_flops(16384, 64, 4)["factor"]
+    assert 2.6 < r < 2.75
