@@ -37,6 +37,7 @@
 #ifndef BDSS_H
 #define BDSS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -139,6 +140,32 @@ bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int6
 /* Description of the last CUDA runtime error that made a bdss_* call on this
  * host thread return BDSS_ERR_CUDA ("no error" if none).  Never NULL. */
 const char *bdss_last_cuda_error(void);
+
+/*
+ * No-allocation variant of bdss_factor_solve (FP64).  The paper has no
+ * counterpart; this entry point exists for callers that may not allocate
+ * device memory while they run: a real-time control or estimation loop in
+ * which cudaMalloc / cudaFree could synchronise the device and take unbounded
+ * time, or a plugin whose host application's allocator owns all device
+ * memory.  It allocates nothing: its workspace is a fixed device array of
+ * BDSS_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that loads
+ * the library holds from load until process exit.
+ *
+ * Arguments are those of bdss_create + bdss_factor_solve for one FP64 system
+ * (same layouts; X may equal B); the call returns after synchronising
+ * `cuda_stream`.  Systems whose workspace (about 3 N n^2 doubles) does not fit
+ * the array are rejected with BDSS_ERR_UNSUPPORTED before anything is
+ * launched.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and sets kernel attributes; make that first
+ * call before any stream capture.  All calls on a device share the one array
+ * and it keeps the last call's contents (the status word is cleared at the
+ * start of each call): calls that overlap on the GPU -- on different streams
+ * or host threads -- race and must be serialised by the caller.
+ */
+#define BDSS_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+bdss_status bdss_factor_solve_noalloc(int64_t N, int32_t n, int32_t d, const double *A_diag,
+                                      const double *A_sub, const double *B, double *X,
+                                      void *cuda_stream, bdss_info *info);
 
 /* Release the handle and its workspace.  NULL-safe. */
 bdss_status bdss_destroy(bdss_handle h);

@@ -39,6 +39,7 @@ SIGNATURES = {
     "bdss_destroy": (_i32, [_vp]),
     "bdss_status_string": (ctypes.c_char_p, [_i32]),
     "bdss_last_cuda_error": (ctypes.c_char_p, []),
+    "bdss_factor_solve_noalloc": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _info_p]),
 }
 
 _lib = None
