@@ -133,6 +133,21 @@ bdss_status bdss_factor_solve(bdss_handle h, const double *A_diag, const double 
  * from the stored factors.  `out` is a host pointer. */
 bdss_status bdss_logdet(bdss_handle h, double *out);
 
+/*
+ * Gradients of a scalar loss L(X), X = A^{-1} B, for a hand-written adjoint
+ * (reverse mode).  Given the adjoint Lambda = A^{-1} dL/dX -- obtained with
+ * bdss_solve on the stored factors, since A is symmetric -- and X, writes
+ *   dA_diag[i] = dL/dA_ii      = -sym(Lambda_i X_i^T)
+ *   dA_sub[i]  = dL/dA_{i+1,i} = -(Lambda_{i+1} X_i^T + X_{i+1} Lambda_i^T)
+ * (dL/dB = Lambda).  Lambda, X: N x n x d device doubles; dA_diag: N x n x n;
+ * dA_sub: (N-1) x n x n (may be NULL iff N == 1).  The operator of Eq. 1 with
+ * sym(A_ii) on the diagonal defines these derivatives; the paper has no
+ * differentiation step.  Needs no factorisation; uses the handle's sizes and
+ * stream.
+ */
+bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double *X, int32_t d,
+                               double *dA_diag, double *dA_sub);
+
 /* Number of grid barriers / kernel launches the last factor or solve issued
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
@@ -140,6 +155,47 @@ bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int6
 /* Description of the last CUDA runtime error that made a bdss_* call on this
  * host thread return BDSS_ERR_CUDA ("no error" if none).  Never NULL. */
 const char *bdss_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Batched solves: K independent systems of uneven N_k and n_k (FP64, d RHS
+ * columns each) -- the batch {A^(k)} of Sec. 3.2 -- factored and solved in
+ * ONE kernel launch.  A device work queue hands out (instance, stage, item
+ * range) tasks; stage s of an instance (its levels' phase A and B, the top
+ * block, the downward levels) starts when stage s-1 of the same instance is
+ * complete, so instances overlap freely.  Per-instance results, status and
+ * latency.  Pointer arrays are HOST arrays of K DEVICE pointers; A_sub_k[k]
+ * may be NULL iff N_k[k] == 1.  1 <= n_k <= 64.
+ * ------------------------------------------------------------------------- */
+typedef struct bdss_batch_ctx *bdss_batch;
+
+/* Allocate the workspace of all instances and build the task queue.  Uses
+ * the autotuned (threads per CTA, items per task) for (max n_k, d) if
+ * bdss_batch_autotune has run in this process, else a default. */
+bdss_status bdss_batch_create(bdss_batch *b, int32_t K, const int64_t *N_k, const int32_t *n_k, int32_t d,
+                              void *cuda_stream);
+/* Bind the K systems' device buffers (X_k[k] may equal B_k[k]).  Synchronises. */
+bdss_status bdss_batch_set_inputs(bdss_batch b, const double *const *A_diag_k, const double *const *A_sub_k,
+                                  const double *const *B_k, double *const *X_k);
+/* Enqueue one factor + solve of every instance on the batch's stream without
+ * waiting.  use_graph != 0: the enqueue sequence (counter resets + the
+ * kernel) is captured once into a CUDA graph and replayed. */
+bdss_status bdss_batch_launch(bdss_batch b, int32_t use_graph);
+/* Wait for the last launch; info_k[k] (K entries, may be NULL) gets the
+ * instance's pivot failure (level/block) with its status code in `reserved`;
+ * latency_us_k[k] (may be NULL) the time from the instance's first task start
+ * to its last task end inside the launch.  Returns the first non-OK status. */
+bdss_status bdss_batch_wait(bdss_batch b, bdss_info *info_k, double *latency_us_k);
+/* Time every candidate (threads per CTA in {32,64,128,256} >= max n_k;
+ * items per task in {1,2,4}) on the bound inputs, keep the fastest for this
+ * batch and record it for (max n_k, d) in the process-wide table. */
+bdss_status bdss_batch_autotune(bdss_batch b, int32_t reps, int32_t *threads, int32_t *items);
+bdss_status bdss_batch_destroy(bdss_batch b);
+
+/* One-shot: create + set_inputs + launch + wait + destroy.  info_k: host, K entries. */
+bdss_status bdss_factor_solve_batched(int32_t K, const int64_t *N_k, const int32_t *n_k, int32_t d,
+                                      const double *const *A_diag_k, const double *const *A_sub_k,
+                                      const double *const *B_k, double *const *X_k, void *cuda_stream,
+                                      bdss_info *info_k);
 
 /*
  * No-allocation variant of bdss_factor_solve (FP64).  The paper has no

@@ -39,6 +39,17 @@ SIGNATURES = {
     "bdss_destroy": (_i32, [_vp]),
     "bdss_status_string": (ctypes.c_char_p, [_i32]),
     "bdss_last_cuda_error": (ctypes.c_char_p, []),
+    "bdss_adjoint_grads": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "bdss_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i32), _i32, _vp]),
+    "bdss_batch_set_inputs": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                     ctypes.POINTER(_vp)]),
+    "bdss_batch_launch": (_i32, [_vp, _i32]),
+    "bdss_batch_wait": (_i32, [_vp, _info_p, ctypes.POINTER(ctypes.c_double)]),
+    "bdss_batch_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "bdss_batch_destroy": (_i32, [_vp]),
+    "bdss_factor_solve_batched": (_i32, [_i32, ctypes.POINTER(_i64), ctypes.POINTER(_i32), _i32,
+                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                         ctypes.POINTER(_vp), _vp, _info_p]),
     "bdss_factor_solve_noalloc": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _info_p]),
 }
 

@@ -445,6 +445,19 @@ bdss_status bdss_logdet(bdss_handle h, double *out) {
   return BDSS_OK;
 }
 
+bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double *X, int32_t d, double *dA_diag,
+                               double *dA_sub) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  if (!Lambda || !X || !dA_diag || !aligned16(Lambda) || !aligned16(X) || !aligned16(dA_diag))
+    return BDSS_ERR_INVALID_ARG;
+  if (h->N > 1 && (!dA_sub || !aligned16(dA_sub))) return BDSS_ERR_INVALID_ARG;
+  if (d < 1 || d > h->d_max) return BDSS_ERR_INVALID_ARG;
+  cudaError_t e = launch_adjoint_grads(h->N, h->n, d, Lambda, X, dA_diag, dA_sub, grid_for(h, h->N) * 2, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return BDSS_OK;
+}
+
 const char *bdss_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda_error); }
 
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers) {

@@ -80,103 +80,100 @@ __global__ void __launch_bounds__(kThreads) k_phaseC(const __grid_constant__ Arg
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual of the refinement loop: R = B - A X, one CTA per block row,
-// one thread per row of the block.  Also max-norms ||R||_inf, ||X||_inf
-// (max over rows of the absolute row sums), accumulated with atomicMax on
-// the bit patterns of non-negative doubles, which order like the values.
-// R is written in FP32 (the right-hand side of the FP32 correction solve).
+// FP64 residual of the refinement loop: R = B - A X, one CTA per block row.
+// sym(A_ii) is staged once in shared memory as S = A_ii + A_ii^T; every
+// thread then owns one (row r, column c) output:
+//   R[r][c] = B[r][c] - 0.5 (S x_i)[r][c] - (A_{i,i-1} x_{i-1})[r][c]
+//                                       - (A_{i+1,i}^T x_{i+1})[r][c]
+// with the two coupling blocks read through L1.  Also the max-norms
+// ||R||_inf and ||X||_inf (max over rows of absolute row sums), accumulated
+// with atomicMax on the bit patterns of non-negative doubles, which order
+// like the values.  R is written in FP32 for the FP32 correction solve.
 // ---------------------------------------------------------------------------
-constexpr int kResMaxD = 16;
-
 __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d, const double *A_diag,
                                                        const double *A_sub, const double *X, const double *B,
                                                        float *R32, DevStatus *st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ld = ldstride(n);
-  double *sD = reinterpret_cast<double *>(smem_raw);  // A_ii (full)
-  double *sS = sD + (size_t)n * ld;                     // A_{i,i-1}
+  double *sS = reinterpret_cast<double *>(smem_raw);  // A_ii + A_ii^T
   double *sX = sS + (size_t)n * ld;                     // x_{i-1}, x_i, x_{i+1}: [3][n][d]
+  double *sR = sX + (size_t)3 * n * d;                  // row sums |R|, |x_i|: [2][n]
   const size_t nn = (size_t)n * n, nd = (size_t)n * d;
   for (long long i = blockIdx.x; i < N; i += gridDim.x) {
-    stage_rows(sD, ld, A_diag + i * nn, n);
-    if (i > 0) stage_rows(sS, ld, A_sub + (i - 1) * nn, n);
+    stage_rows(sS, ld, A_diag + i * nn, n);
     for (int e = threadIdx.x; e < 3 * n * d; e += blockDim.x) {
       const int w = e / (n * d), rem = e - w * n * d;
       const long long blk = i - 1 + w;
       sX[e] = (blk >= 0 && blk < N) ? ldcg(X + blk * nd + rem) : 0.0;
     }
+    for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) sR[e] = 0.0;
     __syncthreads();
-    const int r = threadIdx.x;
-    if (r < n) {
-      double rs = 0.0, xs = 0.0;  // absolute row sums of R and X over all d columns
-      for (int c0 = 0; c0 < d; c0 += kResMaxD) {
-        const int dc = min(kResMaxD, d - c0);
-        double accD[kResMaxD], acc[kResMaxD];
-#pragma unroll
-        for (int c = 0; c < kResMaxD; ++c) { accD[c] = 0.0; acc[c] = 0.0; }
-        const double *xm = sX, *x0 = sX + nd, *xp = sX + 2 * nd;
-        // sym(A_ii) x_i = 0.5 * sum_p (A[r][p] + A[p][r]) x_p
-        for (int p = 0; p < n; ++p) {
-          const double sp = sD[r * ld + p] + sD[p * ld + r];
-#pragma unroll
-          for (int c = 0; c < kResMaxD; ++c)
-            if (c < dc) accD[c] = fma(sp, x0[p * d + c0 + c], accD[c]);
-        }
-        if (i > 0)
-          for (int p = 0; p < n; ++p) {
-            const double a = sS[r * ld + p];
-#pragma unroll
-            for (int c = 0; c < kResMaxD; ++c)
-              if (c < dc) acc[c] = fma(a, xm[p * d + c0 + c], acc[c]);
-          }
-        if (i + 1 < N) {
-          const double *Au = A_sub + i * nn;  // A_{i+1,i}^T: element (r,p) = Au[p][r]
-          for (int p = 0; p < n; ++p) {
-            const double a = ldcg(Au + (size_t)p * n + r);
-#pragma unroll
-            for (int c = 0; c < kResMaxD; ++c)
-              if (c < dc) acc[c] = fma(a, xp[p * d + c0 + c], acc[c]);
-          }
-        }
-        const double *Bi = B + i * nd + (size_t)r * d + c0;
-        float *Ri = R32 + i * nd + (size_t)r * d + c0;
-#pragma unroll
-        for (int c = 0; c < kResMaxD; ++c)
-          if (c < dc) {
-            const double rv = (ldcg(Bi + c) - acc[c]) - 0.5 * accD[c];
-            Ri[c] = (float)rv;
-            rs += fabs(rv);
-            xs += fabs(x0[r * d + c0 + c]);
-          }
+    // S = A + A^T in place: each unordered pair (r, p) belongs to one thread
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, p = e - r * n;
+      if (p <= r) {
+        const double v = sS[r * ld + p] + sS[p * ld + r];
+        sS[r * ld + p] = v;
+        sS[p * ld + r] = v;
       }
-      atomicMax(&st->nrm[0], (unsigned long long)__double_as_longlong(rs));
-      atomicMax(&st->nrm[1], (unsigned long long)__double_as_longlong(xs));
+    }
+    __syncthreads();
+    const double *xm = sX, *x0 = sX + nd, *xp = sX + 2 * nd;
+    const double *Al = A_sub + (i - 1) * nn;  // A_{i,i-1} (valid when i > 0)
+    const double *Au = A_sub + i * nn;        // A_{i+1,i} (valid when i + 1 < N)
+    for (int t = threadIdx.x; t < n * d; t += blockDim.x) {
+      const int r = t / d, c = t - r * d;
+      double accD = 0.0, acc = 0.0;
+      const double *Sr = sS + r * ld;
+      for (int p = 0; p < n; ++p) accD = fma(Sr[p], x0[p * d + c], accD);
+      if (i > 0)
+        for (int p = 0; p < n; ++p) acc = fma(__ldg(Al + (size_t)r * n + p), xm[p * d + c], acc);
+      if (i + 1 < N)
+        for (int p = 0; p < n; ++p) acc = fma(__ldg(Au + (size_t)p * n + r), xp[p * d + c], acc);
+      const double rv = (ldcg(B + i * nd + t) - acc) - 0.5 * accD;
+      R32[i * nd + t] = (float)rv;
+      atomicAdd(&sR[r], fabs(rv));
+      atomicAdd(&sR[n + r], fabs(x0[t]));
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      atomicMax(&st->nrm[0], (unsigned long long)__double_as_longlong(sR[r]));
+      atomicMax(&st->nrm[1], (unsigned long long)__double_as_longlong(sR[n + r]));
     }
     __syncthreads();
   }
 }
 
-// ||A||_inf of the full operator: one CTA per block row, thread per row.
+// ||A||_inf of the full operator: one CTA per block row; each row's absolute
+// sum is split over kNormSplit threads and combined in shared memory.
+constexpr int kNormSplit = 4;
+
 __global__ void __launch_bounds__(kThreads) k_norm_A(long long N, int n, const double *A_diag,
                                                      const double *A_sub, DevStatus *st) {
+  __shared__ double rs[kThreads];
   const size_t nn = (size_t)n * n;
   for (long long i = blockIdx.x; i < N; i += gridDim.x) {
-    const int r = threadIdx.x;
-    if (r < n) {
-      double s = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) rs[r] = 0.0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * kNormSplit; t += blockDim.x) {
+      const int r = t / kNormSplit, q = t - r * kNormSplit;
+      double s = 0.0, sd = 0.0;
       const double *D = A_diag + i * nn;
-      for (int p = 0; p < n; ++p) s += fabs(ldcg(D + r * n + p) + ldcg(D + p * n + r));
-      s *= 0.5;
+      for (int p = q; p < n; p += kNormSplit) sd += fabs(__ldg(D + (size_t)r * n + p) + __ldg(D + (size_t)p * n + r));
       if (i > 0) {
         const double *S = A_sub + (i - 1) * nn;
-        for (int p = 0; p < n; ++p) s += fabs(ldcg(S + r * n + p));
+        for (int p = q; p < n; p += kNormSplit) s += fabs(__ldg(S + (size_t)r * n + p));
       }
       if (i + 1 < N) {
         const double *S = A_sub + i * nn;
-        for (int p = 0; p < n; ++p) s += fabs(ldcg(S + (size_t)p * n + r));
+        for (int p = q; p < n; p += kNormSplit) s += fabs(__ldg(S + (size_t)p * n + r));
       }
-      atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong(s));
+      atomicAdd(&rs[r], fma(0.5, sd, s));
     }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong(rs[r]));
+    __syncthreads();
   }
 }
 
@@ -205,6 +202,57 @@ __global__ void __launch_bounds__(kThreads) k_logdet(long long N, int n, const T
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// Adjoint gradients of a scalar loss through X = A^{-1} B, given
+// Lambda = A^{-1} dL/dX (one CTA per block row, one thread per entry):
+//   dL/dA_ii      = -sym(Lambda_i X_i^T)
+//   dL/dA_{i+1,i} = -(Lambda_{i+1} X_i^T + X_{i+1} Lambda_i^T)
+// (the diagonal blocks enter the operator as sym(A_ii); A_{i+1,i} enters at
+// (i+1, i) and, transposed, at (i, i+1)).
+__global__ void __launch_bounds__(kThreads) k_adjoint_grads(long long N, int n, int d, const double *Lam,
+                                                            const double *X, double *dA_diag, double *dA_sub) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *sL0 = reinterpret_cast<double *>(smem_raw);  // Lambda_i   [n][d]
+  double *sX0 = sL0 + (size_t)n * d;                    // X_i
+  double *sL1 = sX0 + (size_t)n * d;                    // Lambda_{i+1}
+  double *sX1 = sL1 + (size_t)n * d;                    // X_{i+1}
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  for (long long i = blockIdx.x; i < N; i += gridDim.x) {
+    const bool next = (i + 1 < N);
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      sL0[e] = ldcg(Lam + i * nd + e);
+      sX0[e] = ldcg(X + i * nd + e);
+      sL1[e] = next ? ldcg(Lam + (i + 1) * nd + e) : 0.0;
+      sX1[e] = next ? ldcg(X + (i + 1) * nd + e) : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      double g = 0.0;
+      for (int k = 0; k < d; ++k) {
+        g = fma(sL0[r * d + k], sX0[c * d + k], g);
+        g = fma(sX0[r * d + k], sL0[c * d + k], g);
+      }
+      dA_diag[i * nn + e] = -0.5 * g;
+      if (next) {
+        double h = 0.0;
+        for (int k = 0; k < d; ++k) {
+          h = fma(sL1[r * d + k], sX0[c * d + k], h);
+          h = fma(sX1[r * d + k], sL0[c * d + k], h);
+        }
+        dA_sub[i * nn + e] = -h;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, const double *X, double *dA_diag,
+                                 double *dA_sub, int grid, cudaStream_t s) {
+  const size_t sm = (size_t)4 * n * d * sizeof(double);
+  k_adjoint_grads<<<grid, kThreads, sm, s>>>(N, n, d, Lam, X, dA_diag, dA_sub);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -230,7 +278,7 @@ static cudaError_t raise_smem_limits() {
       (const void *)k_persistent<double>, (const void *)k_phaseA<double>, (const void *)k_phaseB<double>,
       (const void *)k_top<double>,        (const void *)k_phaseC<double>, (const void *)k_persistent<float>,
       (const void *)k_phaseA<float>,      (const void *)k_phaseB<float>,  (const void *)k_top<float>,
-      (const void *)k_phaseC<float>,      (const void *)k_residual};
+      (const void *)k_phaseC<float>,      (const void *)k_residual,       (const void *)k_adjoint_grads};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, k);
@@ -286,7 +334,7 @@ cudaError_t launch_phaseC(const Args<T> &a, int l, int grid, size_t smem, cudaSt
 
 cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
                             const double *B, float *R32, DevStatus *st, int grid, cudaStream_t s) {
-  const size_t sm = ((size_t)2 * n * ldstride(n) + (size_t)3 * n * d) * sizeof(double);
+  const size_t sm = ((size_t)n * ldstride(n) + (size_t)3 * n * d + (size_t)2 * n) * sizeof(double);
   k_residual<<<grid, kThreads, sm, s>>>(N, n, d, A_diag, A_sub, X, B, R32, st);
   return cudaGetLastError();
 }

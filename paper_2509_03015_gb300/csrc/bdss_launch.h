@@ -22,6 +22,8 @@ cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, d
                           cudaStream_t s);
 cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
                             const double *B, float *R32, DevStatus *st, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, const double *X, double *dA_diag,
+                                 double *dA_sub, int grid, cudaStream_t s);
 cudaError_t launch_norm_A(long long N, int n, const double *A_diag, const double *A_sub, DevStatus *st, int grid,
                           cudaStream_t s);
 

@@ -92,6 +92,18 @@ class Solver:
         self.last_info = info
         return X
 
+    def adjoint_grads(self, Lam, X):
+        """dL/dA_diag, dL/dA_sub from the adjoint Lam = A^-1 dL/dX and X."""
+        _check_tensor(Lam, "Lambda")
+        _check_tensor(X, "X", tuple(Lam.shape))
+        d = X.shape[-1]
+        dA_diag = torch.empty((self.N, self.n, self.n), dtype=torch.float64, device=X.device)
+        dA_sub = torch.empty((max(self.N - 1, 0), self.n, self.n), dtype=torch.float64, device=X.device)
+        st = self.lib.bdss_adjoint_grads(self.h, _ptr(Lam), _ptr(X), d, _ptr(dA_diag),
+                                         _ptr(dA_sub if self.N > 1 else None))
+        _lib.check(st, "bdss_adjoint_grads")
+        return dA_diag, dA_sub
+
     def logdet(self):
         out = ctypes.c_double()
         _lib.check(self.lib.bdss_logdet(self.h, ctypes.byref(out)), "bdss_logdet")
@@ -122,3 +134,103 @@ def solve(A_diag, A_sub, B, precision="fp64"):
         return s.factor_solve(A_diag, A_sub, B)
     finally:
         s.close()
+
+
+class BlockTriSolve(torch.autograd.Function):
+    """X = A^{-1} B for the SPD block-tridiagonal A(A_diag, A_sub), FP64.
+
+    forward:  factor + solve (one persistent launch); the factors stay in a
+              handle saved for backward.
+    backward: the adjoint solve A Lam = dL/dX reuses the stored factors (A is
+              symmetric), then dL/dB = Lam, dL/dA_ii = -sym(Lam_i X_i^T),
+              dL/dA_{i+1,i} = -(Lam_{i+1} X_i^T + X_{i+1} Lam_i^T)."""
+
+    @staticmethod
+    def forward(ctx, A_diag, A_sub, B):
+        N, n, _ = A_diag.shape
+        d = B.shape[-1]
+        solver = Solver(N, n, d_max=d, precision="fp64")
+        X = solver.factor_solve(A_diag.contiguous(), A_sub.contiguous(), B.contiguous())
+        ctx.solver = solver
+        ctx.save_for_backward(X)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        (X,) = ctx.saved_tensors
+        solver = ctx.solver
+        Lam = solver.solve(gX.contiguous())
+        dA_diag, dA_sub = solver.adjoint_grads(Lam, X)
+        solver.close()
+        ctx.solver = None
+        return dA_diag, dA_sub, Lam
+
+
+def block_tri_solve(A_diag, A_sub, B):
+    """Differentiable X = A^{-1} B (see BlockTriSolve)."""
+    return BlockTriSolve.apply(A_diag, A_sub, B)
+
+
+class BatchSolver:
+    """K independent FP64 systems of uneven (N_k, n_k), factored and solved in
+    one launch (device work queue).  `systems` is a list of (A_diag, A_sub,
+    B) CUDA float64 tensors; X_k are allocated unless given."""
+
+    def __init__(self, systems, X=None, stream=None, autotune=0):
+        self.lib = _lib.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        K = len(systems)
+        self.K = K
+        self.systems = systems
+        d = systems[0][2].shape[-1]
+        Nk = (ctypes.c_int64 * K)(*[int(s[0].shape[0]) for s in systems])
+        nk = (ctypes.c_int32 * K)(*[int(s[0].shape[1]) for s in systems])
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.bdss_batch_create(ctypes.byref(h), K, Nk, nk, d, ctypes.c_void_p(self.stream.cuda_stream)),
+                   "bdss_batch_create")
+        self.h = h
+        self.X = X if X is not None else [torch.empty_like(s[2]) for s in systems]
+        arr = lambda ts: (ctypes.c_void_p * K)(*[t.data_ptr() if t is not None and t.numel() else None for t in ts])
+        for (Ad, As, B), Xk in zip(systems, self.X):
+            _check_tensor(Ad, "A_diag")
+            _check_tensor(B, "B")
+            _check_tensor(Xk, "X", tuple(B.shape))
+            if Ad.shape[0] > 1:
+                _check_tensor(As, "A_sub")
+        _lib.check(self.lib.bdss_batch_set_inputs(self.h, arr([s[0] for s in systems]), arr([s[1] for s in systems]),
+                                                  arr([s[2] for s in systems]), arr(self.X)), "bdss_batch_set_inputs")
+        self.config = None
+        if autotune:
+            t, i = ctypes.c_int32(), ctypes.c_int32()
+            _lib.check(self.lib.bdss_batch_autotune(self.h, int(autotune), ctypes.byref(t), ctypes.byref(i)),
+                       "bdss_batch_autotune")
+            self.config = (t.value, i.value)
+
+    def launch(self, graph=False):
+        _lib.check(self.lib.bdss_batch_launch(self.h, 1 if graph else 0), "bdss_batch_launch")
+
+    def wait(self, raise_on_error=True):
+        """Returns (per-instance status list, per-instance latency in us)."""
+        info = (_lib.bdss_info * self.K)()
+        lat = (ctypes.c_double * self.K)()
+        st = self.lib.bdss_batch_wait(self.h, info, lat)
+        self.info = info
+        if raise_on_error:
+            _lib.check(st, "bdss_batch_wait")
+        return [info[k].reserved for k in range(self.K)], [lat[k] for k in range(self.K)]
+
+    def run(self, graph=False):
+        self.launch(graph)
+        self.wait()
+        return self.X
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bdss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
