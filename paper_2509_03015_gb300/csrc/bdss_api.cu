@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "../../include/bdss.h"
@@ -25,8 +26,10 @@ struct bdss_ctx {
   int bps = 0;          // resident CTAs per SM of the persistent kernel
   size_t smem = 0;      // dynamic shared memory per CTA
   // workspace
+  bool large = false;   // 64 < n <= 256: tiled path
   void *Ld = nullptr;   // N n n  (T)
   void *Wb = nullptr;   // coupling slots (T)
+  void *Eb = nullptr;   // large path: couplings of levels >= 1 (T)
   double *Ltop = nullptr;
   float *Y32 = nullptr;  // mixed: working RHS / correction (N n d_max)
   float *R32 = nullptr;  // mixed: FP32 residual (N n d_max)
@@ -108,6 +111,7 @@ static Args<T> base_args(bdss_ctx *h) {
   a.p = h->plan;
   a.Ld = (T *)h->Ld;
   a.Wb = (T *)h->Wb;
+  a.Eb = (T *)h->Eb;
   a.Ltop = h->Ltop;
   a.st = h->dst;
   a.timeout_ns = h->timeout_ns;
@@ -116,9 +120,45 @@ static Args<T> base_args(bdss_ctx *h) {
 }
 
 // One factor and/or RHS pass over all levels, persistent or per level.
+// Large-block path: three tile sub-phases per level (see bdss_large.cu).
+template <typename T>
+static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, bool rhs) {
+  const Plan &p = h->plan;
+  const int esz = (int)sizeof(T);
+  if (h->persistent) {
+    long long most = 1;
+    for (int l = 0; l < p.L; ++l)
+      for (int sub = 0; sub < 4; ++sub) {
+        const long long t = large_sub_tasks(p, l, sub, factor ? 1 : 0, rhs ? a.d : 0, esz);
+        if (t > most) most = t;
+      }
+    h->launches += 1;
+    h->barriers += (factor ? 3 : 2) * p.L + ((rhs && p.L > 0) ? p.L : 0);
+    return launch_large_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid_for(h, most), h->smem, h->stream);
+  }
+  Args<T> b = a;
+  if (!rhs) b.d = 0;
+  const int f = factor ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < p.L && e == cudaSuccess; ++l)
+    for (int sub = factor ? 0 : 1; sub < 3 && e == cudaSuccess; ++sub) {
+      e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz)), h->smem, h->stream);
+      h->launches += 1;
+    }
+  if (e == cudaSuccess) e = launch_large_top<T>(b, f, h->smem, h->stream);
+  h->launches += 1;
+  if (rhs)
+    for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
+      e = launch_large_sub<T>(b, l, 3, 0, grid_for(h, large_sub_tasks(p, l, 3, 0, b.d, esz)), h->smem, h->stream);
+      h->launches += 1;
+    }
+  return e;
+}
+
 template <typename T>
 static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool rhs) {
   const Plan &p = h->plan;
+  if (h->large) return run_levels_large<T>(h, a, factor, rhs);
   if (h->persistent) {
     const int grid = grid_for(h, (p.N + 1) / 2);
     h->launches += 1;
@@ -168,6 +208,7 @@ bdss_status bdss_destroy(bdss_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->Ld);
   cudaFree(h->Wb);
+  cudaFree(h->Eb);
   cudaFree(h->Ltop);
   cudaFree(h->Y32);
   cudaFree(h->R32);
@@ -184,7 +225,7 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
   *out = nullptr;
   if (N < 1 || n < 1 || d_max < 1 || d_max > 64) return BDSS_ERR_INVALID_ARG;
   if (prec != BDSS_FP64 && prec != BDSS_FP32_IR && prec != BDSS_TF32_IR) return BDSS_ERR_INVALID_ARG;
-  if (n > kMaxN) return BDSS_ERR_UNSUPPORTED;
+  if (n > kMaxNLarge) return BDSS_ERR_UNSUPPORTED;
   if (N > ((int64_t)1 << (kMaxLevels - 2))) return BDSS_ERR_UNSUPPORTED;
   bdss_ctx *h = new (std::nothrow) bdss_ctx();
   if (!h) return BDSS_ERR_ALLOC;
@@ -201,14 +242,25 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) { bdss_destroy(h); return cuda_fail(e); }
   const size_t esz = is_mixed(h) ? sizeof(float) : sizeof(double);
-  const size_t need = is_mixed(h) ? smem_bytes<float>(n, d_max) : smem_bytes<double>(n, d_max);
+  h->large = n > kMaxN;
+  size_t need;
+  if (h->large) need = is_mixed(h) ? smem_bytes_large<float>(n, d_max) : smem_bytes_large<double>(n, d_max);
+  else need = is_mixed(h) ? smem_bytes<float>(n, d_max) : smem_bytes<double>(n, d_max);
   if (need > (size_t)smem_optin) { bdss_destroy(h); return BDSS_ERR_UNSUPPORTED; }
-  e = is_mixed(h) ? configure<float>(n, d_max, &h->smem, &h->bps) : configure<double>(n, d_max, &h->smem, &h->bps);
+  if (h->large) {
+    e = configure<double>(1, 1, &h->smem, &h->bps);  // raises every kernel's shared-memory limit
+    if (e == cudaSuccess)
+      e = is_mixed(h) ? configure_large<float>(n, d_max, &h->smem, &h->bps)
+                      : configure_large<double>(n, d_max, &h->smem, &h->bps);
+  } else {
+    e = is_mixed(h) ? configure<float>(n, d_max, &h->smem, &h->bps) : configure<double>(n, d_max, &h->smem, &h->bps);
+  }
   if (e != cudaSuccess || h->bps < 1) { bdss_destroy(h); return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration); }
   const size_t nn = (size_t)n * n;
   const size_t slots = (size_t)(h->plan.off[h->plan.L] > 0 ? h->plan.off[h->plan.L] : 1);
   bool ok = cudaMalloc(&h->Ld, (size_t)N * nn * esz) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Wb, slots * nn * esz) == cudaSuccess;
+  if (h->large) ok = ok && cudaMalloc(&h->Eb, slots * nn * esz) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&h->Ltop, nn * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&h->partial, kLogdetGrid * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&h->dst, sizeof(DevStatus)) == cudaSuccess;
@@ -334,8 +386,10 @@ static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_i
   for (int it = 0;; ++it) {
     cudaError_t e = reset_status(h);
     if (e == cudaSuccess)
-      e = launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, grid_for(h, h->N) * 2,
-                          h->stream);
+      e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst,
+                                          (int)std::min<long long>(h->N, 2LL * h->sms), h->stream)
+                   : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst,
+                                     grid_for(h, h->N) * 2, h->stream);
     h->launches += 1;
     if (e != cudaSuccess) return cuda_fail(e);
     bdss_status st = finish(h, nullptr);

@@ -56,6 +56,8 @@ struct Args {
   const double *A_sub;
   T *Ld;
   T *Wb;
+  T *Eb;                 // large-block path: couplings S_{k+1,k} of levels >= 1,
+                         // kept apart from Wb (several tasks share one block)
   double *Ltop;
   int d;                 // right-hand-side columns in this call (0: none)
   const double *B64;     // level-0 RHS source in FP64, or null

@@ -1,0 +1,523 @@
+// Large-block path (64 < n <= 256): the same odd-even reduction and storage
+// as the shared-memory path (bdss_device.cuh), with every n x n operation cut
+// into 64 x 64 tiles staged through shared memory, so that one block's work
+// can be spread over tile tasks:
+//   A1  eliminated block: blocked right-looking Cholesky, in place in Ld
+//       (Algorithm 1, potrf; level 0 reads sym(A_jj) on its first step);
+//   A2  (eliminated block, vector tile): forward substitution of the coupling
+//       vectors (W_L, W_R, Sec. 3.3 stage 2) and of the RHS (y = L^{-1} b),
+//       blocked by 64-row tiles (gemm update + triangular tile solve);
+//   B   (separator, output tile): Schur update and new coupling (Algorithm 3,
+//       Eq. 5) and the separator RHS update (Algorithm 5);
+//   C   eliminated block: x = L^{-T}(y - W_L x_{j-1} - W_R x_{j+1})
+//       (Algorithms 6, 2), blocked from the bottom tile up;
+//   top the remaining block, FP64, blocked, in Ltop.
+#pragma once
+#include "bdss_device.cuh"
+
+namespace bdss {
+
+constexpr int kTile = 64;   // output / triangular tile
+constexpr int kKc = 32;     // k-chunk staged per gemm step
+constexpr int kTilePad = kTile + 1;
+
+__host__ __device__ inline int ntiles(int n) { return (n + kTile - 1) / kTile; }
+__host__ __device__ inline int vec_tile(int elem_size) { return elem_size == 8 ? 32 : 64; }
+
+// Strided matrix view: element (r, c) at p[r * rs + c * cs]; zero outside
+// rows x cols.  Global views load through L2 (written by other CTAs across
+// grid barriers); shared-memory views (kSmem) load directly.
+template <typename S, bool kSmem = false>
+struct View {
+  const S *p;
+  long long rs, cs;
+  int rows, cols;
+  __device__ S at(int r, int c) const {
+    if (r >= rows || c >= cols) return S(0);
+    const S *q = p + (long long)r * rs + (long long)c * cs;
+    return kSmem ? *q : ldcg(q);
+  }
+};
+
+// acc[i][j] += sum_k A(r0 + 4 tm + i, k) * B(c0 + 4 tn + j, k) for the 64 x 64
+// output tile at (r0, c0), k over [0, K): "NT" products of two strided views
+// through shared memory (sA, sB: kKc x kTilePad each).  256 threads: thread t
+// owns rows 4 (t / 16) + i and columns 4 (t % 16) + j.
+template <typename T, typename VA, typename VB>
+__device__ void gemm_nt_tile(T (&acc)[4][4], const VA &A, int r0, const VB &B, int c0, int K, T *sA, T *sB) {
+  const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+    for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
+      const int m = e / kKc, k = e - m * kKc;
+      const bool kin = (k0 + k) < K;
+      sA[k * kTilePad + m] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
+      sB[k * kTilePad + m] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
+    }
+    __syncthreads();
+    const int kc = min(kKc, K - k0);
+    for (int k = 0; k < kc; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = sA[k * kTilePad + 4 * tm + i];
+        b[i] = sB[k * kTilePad + 4 * tn + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory (in elements of T) of the large-path tasks.
+__host__ __device__ inline size_t smem_large(int n, int d, int esz) {
+  const size_t gemm = (size_t)2 * kKc * kTilePad;
+  const size_t tile = (size_t)kTile * kTilePad;
+  const int vt = vec_tile(esz);
+  const size_t a2 = (size_t)vt * (n + 1) + tile + gemm;   // vectors + L tile + gemm staging
+  const size_t c = (size_t)(d > 0 ? d : 1) * (n + 1) + tile + gemm;
+  const size_t a1 = tile + gemm;
+  size_t m = a2 > c ? a2 : c;
+  if (a1 > m) m = a1;
+  return m + 16;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Cholesky of the n x n matrix M (row-major, leading dim n), in place
+// (lower triangle; diagonal tiles get 1 / L_kk on their diagonal).  `src` is
+// where the not-yet-touched tiles live before the first step (sym(A) from the
+// caller's FP64 block at level 0, else M itself).  Returns 0 or a failing
+// column + 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_flag) {
+  const int nt = ntiles(n);
+  T *sT = smem;                              // 64 x 65 tile
+  T *sA = sT + kTile * kTilePad;
+  T *sB = sA + kKc * kTilePad;
+  const int ld = kTilePad;
+  auto src = [&](int r, int c) -> T {      // element of the matrix before step 0
+    if (src_sym) return T(0.5) * ((T)ldcg(src_sym + (long long)r * n + c) + (T)ldcg(src_sym + (long long)c * n + r));
+    return ldcg(M + (long long)r * n + c);
+  };
+  for (int k = 0; k < nt; ++k) {
+    const int k0 = k * kTile, kb = min(kTile, n - k0);
+    const bool first = (k == 0) && src_sym;
+    // diagonal tile
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int r = e / kTile, c = e - r * kTile;
+      T v = T(0);
+      if (r < kb && c <= r) v = first ? src(k0 + r, k0 + c) : ldcg(M + (long long)(k0 + r) * n + k0 + c);
+      sT[r * ld + c] = v;
+    }
+    __syncthreads();
+    const int bad = chol_staged(sT, ld, kb, s_flag);
+    if (bad) return k0 + bad;
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int r = e / kb, c = e - r * kb;
+      if (c <= r) M[(long long)(k0 + r) * n + k0 + c] = sT[r * ld + c];
+    }
+    // panel below: L_ik = S_ik L_kk^{-T}: each row x solves L_kk x = s
+    for (int i = k + 1; i < nt; ++i) {
+      const int i0 = i * kTile, ib = min(kTile, n - i0);
+      // reuse the gemm staging area for the panel rows (ib x kb)
+      T *sP = sA;  // needs kTile x kTilePad: sA and sB are contiguous 2 * kKc * kTilePad = kTile * kTilePad
+      __syncthreads();
+      for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = e / kTile, c = e - r * kTile;
+        T v = T(0);
+        if (r < ib && c < kb) v = first ? src(i0 + r, k0 + c) : ldcg(M + (long long)(i0 + r) * n + k0 + c);
+        sP[r * ld + c] = v;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < ib; r += blockDim.x) {
+        T *w = sP + r * ld;
+        for (int q = 0; q < kb; ++q) {
+          T acc = w[q];
+          const T *lq = sT + q * ld;
+          for (int p = 0; p < q; ++p) acc = fma(-lq[p], w[p], acc);
+          w[q] = acc * lq[q];
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < ib * kb; e += blockDim.x) {
+        const int r = e / kb, c = e - r * kb;
+        M[(long long)(i0 + r) * n + k0 + c] = sP[r * ld + c];
+      }
+    }
+    __syncthreads();
+    // trailing update: S_ij -= L_ik L_jk^T, k < j <= i
+    for (int i = k + 1; i < nt; ++i)
+      for (int j = k + 1; j <= i; ++j) {
+        const int i0 = i * kTile, j0 = j * kTile;
+        T acc[4][4] = {};
+        const View<T> Ar{M + (long long)k0, n, 1, n, kb};
+        gemm_nt_tile(acc, Ar, i0, Ar, j0, kb, sA, sB);
+        const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = i0 + 4 * tm + a, c = j0 + 4 * tn + b;
+            if (r < n && c < n && c <= r) {
+              const T base = first ? src(r, c) : ldcg(M + (long long)r * n + c);
+              M[(long long)r * n + c] = base - acc[a][b];
+            }
+          }
+        __syncthreads();
+      }
+  }
+  return 0;
+}
+
+// Forward substitution L v = v for `nv` vectors held as rows of sV (stride
+// n + 1), L (n x n, reciprocal diagonal) in global memory, blocked by 64-row
+// tiles: gemm update from the solved rows, then the triangular tile.
+template <typename T>
+__device__ void trsv_fwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
+  const int nt = ntiles(n), lv = n + 1;
+  T *sT = smem;
+  T *sA = sT + kTile * kTilePad;
+  T *sB = sA + kKc * kTilePad;
+  for (int R = 0; R < nt; ++R) {
+    const int r0 = R * kTile, rb = min(kTile, n - r0);
+    if (R > 0) {
+      // sV[c][r0 + r] -= sum_{p < r0} L[r0 + r][p] sV[c][p]; output 64 rows x (up to 64) vectors
+      for (int c0 = 0; c0 < nv; c0 += kTile) {
+        T acc[4][4] = {};
+        const View<T> Lr{L, n, 1, n, r0};
+        const View<T, true> Vc{sV + (long long)c0 * lv, lv, 1, nv - c0, r0};
+        gemm_nt_tile(acc, Lr, r0, Vc, 0, r0, sA, sB);
+        const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = 4 * tm + a, c = c0 + 4 * tn + b;
+            if (r < rb && c < nv) sV[(long long)c * lv + r0 + r] -= acc[a][b];
+          }
+        __syncthreads();
+      }
+    }
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int r = e / kTile, c = e - r * kTile;
+      sT[r * kTilePad + c] = (r < rb && c <= r) ? ldcg(L + (long long)(r0 + r) * n + r0 + c) : T(0);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      T *w = sV + (long long)v * lv + r0;
+      for (int r = 0; r < rb; ++r) {
+        T acc = w[r];
+        const T *lr = sT + r * kTilePad;
+        for (int p = 0; p < r; ++p) acc = fma(-lr[p], w[p], acc);
+        w[r] = acc * lr[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Backward substitution L^T z = t for `nv` vectors (rows of sV), blocked
+// from the bottom tile up.
+template <typename T>
+__device__ void trsv_bwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
+  const int nt = ntiles(n), lv = n + 1;
+  T *sT = smem;
+  T *sA = sT + kTile * kTilePad;
+  T *sB = sA + kKc * kTilePad;
+  for (int R = nt - 1; R >= 0; --R) {
+    const int r0 = R * kTile, rb = min(kTile, n - r0), r1 = r0 + rb;
+    if (r1 < n) {
+      // sV[c][r0 + r] -= sum_{p >= r1} L[p][r0 + r] sV[c][p]
+      for (int c0 = 0; c0 < nv; c0 += kTile) {
+        T acc[4][4] = {};
+        const View<T> Lt{L + (long long)r1 * n, 1, n, n, n - r1};  // (r, k) -> L[r1 + k][r]
+        const View<T, true> Vc{sV + (long long)c0 * lv + r1, lv, 1, nv - c0, n - r1};
+        gemm_nt_tile(acc, Lt, r0, Vc, 0, n - r1, sA, sB);
+        const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = 4 * tm + a, c = c0 + 4 * tn + b;
+            if (r < rb && c < nv) sV[(long long)c * lv + r0 + r] -= acc[a][b];
+          }
+        __syncthreads();
+      }
+    }
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int r = e / kTile, c = e - r * kTile;
+      sT[r * kTilePad + c] = (r < rb && c <= r) ? ldcg(L + (long long)(r0 + r) * n + r0 + c) : T(0);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      T *w = sV + (long long)v * lv + r0;
+      for (int r = rb - 1; r >= 0; --r) {
+        T acc = w[r];
+        for (int p = r + 1; p < rb; ++p) acc = fma(-sT[p * kTilePad + r], w[p], acc);
+        w[r] = acc * sT[r * kTilePad + r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tasks
+// ---------------------------------------------------------------------------
+
+// A1: Cholesky of eliminated position j of level l.
+template <typename T>
+__device__ bool largeA1(const Args<T> &a, int l, long long j, T *smem, int *s_flag) {
+  const int n = a.p.n;
+  const long long orig = j << l;
+  T *M = a.Ld + orig * (long long)n * n;
+  const int bad = chol_blocked(M, n, l == 0 ? a.A_diag + orig * (long long)n * n : nullptr, smem, s_flag);
+  if (bad) {
+    if (threadIdx.x == 0) set_status(a.st, kStNotSPD, l, orig);
+    __syncthreads();
+    return false;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Number of vectors of eliminated position j's forward substitution.
+template <typename T>
+__device__ __forceinline__ int largeA2_vectors(const Args<T> &a, int l, long long j, bool factor) {
+  const int n = a.p.n;
+  const bool hasR = (j + 1 < a.p.Nl[l]);
+  return (factor ? (hasR ? 2 * n : n) : 0) + a.d;
+}
+
+// A2: vector tile v of eliminated position j: vectors are E_L's columns,
+// E_R's rows (if any), then the RHS columns.
+template <typename T>
+__device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor, T *smem) {
+  const int n = a.p.n, d = a.d, lv = n + 1;
+  const long long Nl = a.p.Nl[l];
+  const bool hasR = (j + 1 < Nl);
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n;
+  const int nW = factor ? (hasR ? 2 * n : n) : 0;
+  const int VT = vec_tile(sizeof(T));
+  const int c0 = v * VT, nv = min(VT, nW + d - c0);
+  T *sV = smem;
+  T *work = sV + (size_t)VT * lv;
+  const T *E = (l == 0) ? nullptr : a.Eb + (size_t)a.p.off[l] * nn;  // couplings formed at level l-1
+  // stage vectors
+  for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
+    const int i = e / nv, cc = e - i * nv, c = c0 + cc;
+    T val;
+    if (c < nW && c < n) {  // column c of A_{j,j-1}
+      val = (l == 0) ? (T)ldcg(a.A_sub + (size_t)(j - 1) * nn + (size_t)i * n + c)
+                     : ldcg(E + (size_t)(j - 1) * nn + (size_t)i * n + c);
+    } else if (c < nW) {  // row c - n of A_{j+1,j}
+      const int r = c - n;
+      val = (l == 0) ? (T)ldcg(a.A_sub + (size_t)j * nn + (size_t)r * n + i) : ldcg(E + (size_t)j * nn + (size_t)r * n + i);
+    } else {  // RHS column
+      const int k = c - nW;
+      const size_t bo = (size_t)orig * n * d + (size_t)i * d + k;
+      if (l == 0 && a.B64) val = (T)ldcg(a.B64 + bo);
+      else if (l == 0 && a.Bt) val = ldcg(a.Bt + bo);
+      else val = ldcg(a.Y + bo);
+    }
+    sV[(size_t)cc * lv + i] = val;
+  }
+  __syncthreads();
+  trsv_fwd_blocked(a.Ld + (size_t)orig * nn, n, sV, nv, work);
+  // write back
+  T *W = a.Wb + (size_t)a.p.off[l] * nn;
+  for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
+    const int cc = e / n, i = e - cc * n, c = c0 + cc;
+    const T val = sV[(size_t)cc * lv + i];
+    if (c < nW && c < n) W[(size_t)(j - 1) * nn + (size_t)c * n + i] = val;
+    else if (c < nW) W[(size_t)j * nn + (size_t)(c - n) * n + i] = val;
+    else a.Y[(size_t)orig * n * d + (size_t)i * d + (c - nW)] = val;
+  }
+  __syncthreads();
+}
+
+// Tiles of a separator's phase-B work.
+__host__ __device__ inline int largeB_tiles(int n, bool factor, int d) {
+  const int nt = ntiles(n);
+  return (factor ? nt * (nt + 1) / 2 + nt * nt : 0) + (d > 0 ? nt : 0);
+}
+
+// B: output tile `t` of separator s = 2k at level l.
+template <typename T>
+__device__ void largeB(const Args<T> &a, int l, long long k, int t, bool factor, T *smem) {
+  const int n = a.p.n, d = a.d, nt = ntiles(n);
+  const long long Nl = a.p.Nl[l];
+  const long long s = 2 * k;
+  const bool hasM = (s >= 2), hasP = (s + 1 < Nl), hasE = (s + 2 < Nl);
+  const long long orig = s << l;
+  const size_t nn = (size_t)n * n;
+  const T *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const View<T> W0{W + (size_t)(s - 1) * nn, n, 1, n, n};   // W_R(s-1)^T
+  const View<T> W1{W + (size_t)s * nn, n, 1, n, n};         // W_L(s+1)^T
+  const View<T> W2{W + (size_t)(s + 1) * nn, n, 1, n, n};   // W_R(s+1)^T
+  T *sA = smem, *sB = sA + kKc * kTilePad;
+  const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+  const int nD = factor ? nt * (nt + 1) / 2 : 0, nE = factor ? nt * nt : 0;
+  if (t < nD) {
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    T acc[4][4] = {};
+    if (hasM) gemm_nt_tile(acc, W0, ti * kTile, W0, tj * kTile, n, sA, sB);
+    if (hasP) gemm_nt_tile(acc, W1, ti * kTile, W1, tj * kTile, n, sA, sB);
+    T *Dg = a.Ld + (size_t)orig * nn;
+    const double *Ag = a.A_diag + (size_t)orig * nn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int r = ti * kTile + 4 * tm + i, c = tj * kTile + 4 * tn + jj;
+        if (r < n && c <= r) {
+          const T base = (l == 0) ? T(0.5) * ((T)ldcg(Ag + (size_t)r * n + c) + (T)ldcg(Ag + (size_t)c * n + r))
+                                  : ldcg(Dg + (size_t)r * n + c);
+          Dg[(size_t)r * n + c] = base - acc[i][jj];
+        }
+      }
+  } else if (t < nD + nE) {
+    if (!hasE) return;
+    const int u = t - nD, ti = u / nt, tj = u - ti * nt;
+    T acc[4][4] = {};
+    gemm_nt_tile(acc, W2, ti * kTile, W1, tj * kTile, n, sA, sB);
+    T *En = a.Eb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int r = ti * kTile + 4 * tm + i, c = tj * kTile + 4 * tn + jj;
+        if (r < n && c < n) En[(size_t)r * n + c] = -acc[i][jj];
+      }
+  } else {
+    const int ti = t - nD - nE;
+    const size_t boff = (size_t)orig * n * d;
+    for (int c0 = 0; c0 < d; c0 += kTile) {
+      T acc[4][4] = {};
+      // y as the "B" operand: (c, q) -> y[q][c]
+      const View<T> Ym{a.Y + (size_t)((s - 1) << l) * n * d + c0, 1, d, d - c0, n};
+      const View<T> Yp{a.Y + (size_t)((s + 1) << l) * n * d + c0, 1, d, d - c0, n};
+      if (hasM) gemm_nt_tile(acc, W0, ti * kTile, Ym, 0, n, sA, sB);
+      if (hasP) gemm_nt_tile(acc, W1, ti * kTile, Yp, 0, n, sA, sB);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int r = ti * kTile + 4 * tm + i, c = c0 + 4 * tn + jj;
+          if (r < n && c < d) {
+            const size_t o = boff + (size_t)r * d + c;
+            T base;
+            if (l == 0 && a.B64) base = (T)ldcg(a.B64 + o);
+            else if (l == 0 && a.Bt) base = ldcg(a.Bt + o);
+            else base = ldcg(a.Y + o);
+            a.Y[o] = base - acc[i][jj];
+          }
+        }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+}
+
+// C: downward pass for eliminated position j of level l.
+template <typename T>
+__device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
+  const int n = a.p.n, d = a.d, lv = n + 1;
+  const long long Nl = a.p.Nl[l];
+  const bool hasR = (j + 1 < Nl);
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  T *sV = smem;                       // d vectors of length n
+  T *work = sV + (size_t)d * lv;
+  T *sA = work + kTile * kTilePad, *sB = sA + kKc * kTilePad;
+  const T *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const T *Yj = a.Y + (size_t)orig * nd;
+  // t[q][c] = y[q][c] - sum_p W_L[q][p] x_{j-1}[p][c] - sum_p W_R[q][p] x_{j+1}[p][c],
+  // W_L[q][p] = Wt_L[p][q]
+  const View<T> WLq{W + (size_t)(j - 1) * nn, 1, n, n, n};
+  const View<T> WRq{W + (size_t)j * nn, 1, n, n, n};
+  const View<T> Xm{a.Y + (size_t)((j - 1) << l) * nd, 1, d, d, n};
+  const View<T> Xp{a.Y + (size_t)((j + 1) << l) * nd, 1, d, d, n};
+  const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+  for (int R = 0; R < ntiles(n); ++R)
+    for (int c0 = 0; c0 < d; c0 += kTile) {
+      T acc[4][4] = {};
+      const View<T> Xmc{Xm.p + c0, 1, d, d - c0, n};
+      const View<T> Xpc{Xp.p + c0, 1, d, d - c0, n};
+      gemm_nt_tile(acc, WLq, R * kTile, Xmc, 0, n, sA, sB);
+      if (hasR) gemm_nt_tile(acc, WRq, R * kTile, Xpc, 0, n, sA, sB);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int q = R * kTile + 4 * tm + i, c = c0 + 4 * tn + jj;
+          if (q < n && c < d) sV[(size_t)c * lv + q] = ldcg(Yj + (size_t)q * d + c) - acc[i][jj];
+        }
+      __syncthreads();
+    }
+  trsv_bwd_blocked(a.Ld + (size_t)orig * nn, n, sV, d, work);
+  T *Yo = a.Y + (size_t)orig * nd;
+  for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+    const int i = e / d, c = e - i * d;
+    const T x = sV[(size_t)c * lv + i];
+    Yo[e] = x;
+    if (a.X64) {
+      double *xo = a.X64 + (size_t)orig * nd + e;
+      *xo = a.x_accumulate ? *xo + (double)x : (double)x;
+    }
+  }
+  __syncthreads();
+}
+
+// Top block in FP64: Ltop <- D (from Ld slot 0, or sym(A_00) if no level),
+// blocked Cholesky in place, then x_0 = L^{-T} L^{-1} b_0.
+template <typename T>
+__device__ bool largeTop(const Args<T> &a, bool factor, double *smem, int *s_flag) {
+  const int n = a.p.n, d = a.d, L = a.p.L, lv = n + 1;
+  const size_t nn = (size_t)n * n;
+  if (factor) {
+    if (L > 0) {
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) a.Ltop[e] = (double)ldcg(a.Ld + e);
+      __syncthreads();
+      __threadfence_block();
+    }
+    const int bad = chol_blocked(a.Ltop, n, L == 0 ? a.A_diag : nullptr, smem, s_flag);
+    if (bad) {
+      if (threadIdx.x == 0) set_status(a.st, kStNotSPD, L, 0);
+      __syncthreads();
+      return false;
+    }
+  }
+  if (d > 0) {
+    double *sV = smem;
+    double *work = sV + (size_t)d * lv;
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int i = e / d, c = e - i * d;
+      double v;
+      if (L == 0 && a.B64) v = ldcg(a.B64 + e);
+      else if (L == 0 && a.Bt) v = (double)ldcg(a.Bt + e);
+      else v = (double)ldcg(a.Y + e);
+      sV[(size_t)c * lv + i] = v;
+    }
+    __syncthreads();
+    trsv_fwd_blocked(a.Ltop, n, sV, d, work);
+    trsv_bwd_blocked(a.Ltop, n, sV, d, work);
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int i = e / d, c = e - i * d;
+      const double x = sV[(size_t)c * lv + i];
+      a.Y[e] = (T)x;
+      if (a.X64) a.X64[e] = a.x_accumulate ? a.X64[e] + x : x;
+    }
+  }
+  __syncthreads();
+  (void)nn;
+  return true;
+}
+
+}  // namespace bdss

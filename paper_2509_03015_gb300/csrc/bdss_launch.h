@@ -27,4 +27,18 @@ cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, c
 cudaError_t launch_norm_A(long long N, int n, const double *A_diag, const double *A_sub, DevStatus *st, int grid,
                           cudaStream_t s);
 
+// large-block path (64 < n <= 256)
+constexpr int kMaxNLarge = 256;
+template <typename T> size_t smem_bytes_large(int n, int d);
+template <typename T> cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm);
+template <typename T>
+cudaError_t launch_large_persistent(const Args<T> &a, int factor, int rhs, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_large_sub(const Args<T> &a, int l, int sub, int factor, int grid, size_t smem, cudaStream_t s);
+template <typename T> cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStream_t s);
+long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz);
+cudaError_t launch_residual_rows(long long N, int n, int d, const double *A_diag, const double *A_sub,
+                                 const double *X, const double *B, float *R32, DevStatus *st, int grid,
+                                 cudaStream_t s);
+
 }  // namespace bdss

@@ -64,7 +64,7 @@ def test_host_argument_checks(lib):
     assert lib.bdss_create(ctypes.byref(h), 10, 8, 65, 0, None) == 1
     assert lib.bdss_create(ctypes.byref(h), 10, 8, 1, 7, None) == 1
     assert lib.bdss_create(None, 10, 8, 1, 0, None) == 1
-    assert lib.bdss_create(ctypes.byref(h), 10, 65, 1, 0, None) == 8  # n > 64 not built yet
+    assert lib.bdss_create(ctypes.byref(h), 10, 257, 1, 0, None) == 8  # n > 256 not supported
     assert h.value is None
     # NULL handles
     assert lib.bdss_destroy(None) == 0
