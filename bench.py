@@ -133,6 +133,83 @@ def cpu_baseline(s, budget_s=10.0):
                       f"scaled by {N}/{Ns}"}
 
 
+def _timed(fn, reps, stream, max_over_ranks):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1)) / reps
+
+
+def other_workloads(dev, stream, world, max_over_ranks, args):
+    """The other hot-path workloads on the same GPU: the N=4096, n=256, d=16
+    mixed-precision system (FP32 + refinement vs FP64), the 512-instance
+    uneven MPC batch in one launch, and forward + adjoint backward at
+    N=2048, n=32, d=8."""
+    import torch
+
+    from paper_2509_03015_gb300 import BatchSolver, Solver, block_tri_solve
+    res = {}
+    reps = max(2, args.steps // 5)
+    # -- mixed precision at n = 256 --------------------------------------------
+    name = "kalman-N4096-n256-d16-rho0.99"
+    cfg = inputs.WORKLOADS[name]
+    s = inputs.workload(name)
+    Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
+    X = torch.empty_like(B)
+    entry = {"N": cfg["N"], "n": cfg["n"], "d": cfg["d"], "rho": cfg["rho"]}
+    tally = accounting.thomas_flops(cfg["N"], cfg["n"], cfg["d"])
+    for prec in ("fp32_ir", "fp64"):
+        sol = Solver(cfg["N"], cfg["n"], d_max=cfg["d"], precision=prec, stream=stream)
+        sol.factor_solve(Ad, As, B, X)
+        ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 1 if prec == "fp64" else reps, stream, max_over_ranks)
+        info = sol.last_info
+        entry[prec] = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms,
+                       "thomas_tflops": (tally["factor"] + tally["solve"]) / (ms * 1e-3) / 1e12,
+                       "refine_iters": info.iters, "backward_err": info.backward_err}
+        sol.close()
+    entry["speedup_fp32_ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["fp32_ir"]["ms_per_step"]
+    res[name] = entry
+    del Ad, As, B, X
+    # -- batched MPC systems -----------------------------------------------------
+    systems = inputs.mpc_batch(K=512, d=1, rho=0.95, seed=0)
+    dev_sys = []
+    for q in systems:
+        N, n, _ = q["A_diag"].shape
+        As_ = q["A_sub"] if N > 1 else np.zeros((1, n, n))
+        dev_sys.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (q["A_diag"], As_, q["B"])))
+    bs = BatchSolver(dev_sys, stream=stream, autotune=1)
+    bs.run(graph=True)
+    ms = _timed(lambda: (bs.launch(graph=True), bs.wait()), reps, stream, max_over_ranks)
+    _, lat = bs.wait()
+    lat = sorted(lat)
+    blocks = sum(q["A_diag"].shape[0] for q in systems)
+    res["mpc-batch-512"] = {"K": 512, "total_blocks": blocks, "value": world * 512 * 1e3 / ms, "unit": "systems/s",
+                            "ms_per_launch": ms, "latency_us_p50": lat[len(lat) // 2],
+                            "latency_us_p99": lat[int(0.99 * (len(lat) - 1))],
+                            "autotuned": {"threads_per_cta": bs.config[0], "items_per_task": bs.config[1]},
+                            "graph": True}
+    bs.close()
+    del dev_sys
+    # -- differentiation -----------------------------------------------------------
+    name = "kalman-N2048-n32-d8-grad"
+    s = inputs.workload(name, with_W=True)
+    W = torch.from_numpy(s["W"]).to(dev)
+    tens = [torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B")]
+
+    def fwd_bwd():
+        a, b_, c = (t.clone().requires_grad_(True) for t in tens)
+        (block_tri_solve(a, b_, c) * W).sum().backward()
+    fwd_bwd()
+    ms = _timed(fwd_bwd, reps, stream, max_over_ranks)
+    res[name] = {"value": world * 1e3 / ms, "unit": "systems/s (forward + backward)", "ms_per_step": ms}
+    return res
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -324,6 +401,9 @@ def main():
         ms4 = max_over_ranks(e0.elapsed_time(e1)) / K4
         out["e2e"] = {"value": world * 1e3 / ms4, "unit": "systems/s", "ms_per_step": ms4,
                       "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": X.numel() * 8}
+
+    if not args.no_extras and args.N is None:
+        out["workloads"] = other_workloads(dev, stream, world, max_over_ranks, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s)

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
 template <typename T>
 size_t smem_bytes_large(int n, int d) {
   size_t b = smem_large(n, d, (int)sizeof(T)) * sizeof(T);
-  const size_t top = smem_large(n, d, 8) * sizeof(double);
+  const size_t top = smem_large_top(n, d) * sizeof(double);
   if (top > b) b = top;
   return (b + 15) & ~(size_t)15;
 }

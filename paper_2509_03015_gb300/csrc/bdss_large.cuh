@@ -71,6 +71,12 @@ __device__ void gemm_nt_tile(T (&acc)[4][4], const VA &A, int r0, const VB &B, i
   }
 }
 
+// Shared memory (in elements of FP64) of the FP64 top block: d solution
+// vectors plus the tile work area (it never stages coupling vectors).
+__host__ __device__ inline size_t smem_large_top(int n, int d) {
+  return (size_t)(d > 0 ? d : 1) * (n + 1) + (size_t)kTile * kTilePad + (size_t)2 * kKc * kTilePad + 16;
+}
+
 // Shared memory (in elements of T) of the large-path tasks.
 __host__ __device__ inline size_t smem_large(int n, int d, int esz) {
   const size_t gemm = (size_t)2 * kKc * kTilePad;
