@@ -163,7 +163,7 @@ def other_workloads(dev, stream, world, max_over_ranks, args):
     X = torch.empty_like(B)
     entry = {"N": cfg["N"], "n": cfg["n"], "d": cfg["d"], "rho": cfg["rho"]}
     tally = accounting.thomas_flops(cfg["N"], cfg["n"], cfg["d"])
-    for prec in ("fp32_ir", "fp64"):
+    for prec in ("tf32_ir", "fp32_ir", "fp64"):
         sol = Solver(cfg["N"], cfg["n"], d_max=cfg["d"], precision=prec, stream=stream)
         sol.factor_solve(Ad, As, B, X)
         ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 1 if prec == "fp64" else reps, stream, max_over_ranks)
@@ -173,6 +173,7 @@ def other_workloads(dev, stream, world, max_over_ranks, args):
                        "refine_iters": info.iters, "backward_err": info.backward_err}
         sol.close()
     entry["speedup_fp32_ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["fp32_ir"]["ms_per_step"]
+    entry["speedup_tf32_ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["tf32_ir"]["ms_per_step"]
     res[name] = entry
     del Ad, As, B, X
     # -- batched MPC systems -----------------------------------------------------

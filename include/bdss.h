@@ -61,7 +61,9 @@ typedef enum {
 typedef enum {
   BDSS_FP64 = 0,     /* every step in FP64 (DFMA) */
   BDSS_FP32_IR = 1,  /* factor/solve in FP32, FP64 residual + iterative refinement */
-  BDSS_TF32_IR = 2   /* as FP32_IR, Schur-update products on TF32 tensor cores */
+  BDSS_TF32_IR = 2   /* as FP32_IR; for 64 < n <= 256 (n % 4 == 0) the Schur-update
+                        products run on tcgen05 tensor cores (3xTF32 split, FP32
+                        accumulation); for n <= 64 it equals BDSS_FP32_IR */
 } bdss_precision;
 
 typedef struct {
@@ -151,6 +153,13 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
 /* Number of grid barriers / kernel launches the last factor or solve issued
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
+
+/* Self-check of the tensor-core Schur tile used by BDSS_TF32_IR for n > 64:
+ * one 128 x 128 tile C = A B^T with K = 256 computed with TMA-fed
+ * tcgen05.mma (3xTF32 split) and compared on the device with an FP64 product
+ * of the same FP32 inputs.  *max_rel_err = max |C_tc - C_ref| / sum_k |a b|
+ * (host pointer).  Allocates and frees its own small buffers. */
+bdss_status bdss_tc_selftest(double *max_rel_err);
 
 /* Description of the last CUDA runtime error that made a bdss_* call on this
  * host thread return BDSS_ERR_CUDA ("no error" if none).  Never NULL. */

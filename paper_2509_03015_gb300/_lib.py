@@ -39,6 +39,7 @@ SIGNATURES = {
     "bdss_destroy": (_i32, [_vp]),
     "bdss_status_string": (ctypes.c_char_p, [_i32]),
     "bdss_last_cuda_error": (ctypes.c_char_p, []),
+    "bdss_tc_selftest": (_i32, [ctypes.POINTER(ctypes.c_double)]),
     "bdss_adjoint_grads": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
     "bdss_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i32), _i32, _vp]),
     "bdss_batch_set_inputs": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),

@@ -30,6 +30,8 @@ struct bdss_ctx {
   void *Ld = nullptr;   // N n n  (T)
   void *Wb = nullptr;   // coupling slots (T)
   void *Eb = nullptr;   // large path: couplings of levels >= 1 (T)
+  int tf32 = 0;         // TF32 mode on the large path: tensor-core Schur tiles
+  CUtensorMap *d_tmap = nullptr;  // TMA map of Wb (device copy)
   double *Ltop = nullptr;
   float *Y32 = nullptr;  // mixed: working RHS / correction (N n d_max)
   float *R32 = nullptr;  // mixed: FP32 residual (N n d_max)
@@ -116,6 +118,8 @@ static Args<T> base_args(bdss_ctx *h) {
   a.st = h->dst;
   a.timeout_ns = h->timeout_ns;
   a.skip_barrier = h->skip_barrier;
+  a.tf32 = h->tf32;
+  a.tmap_w = h->d_tmap;
   return a;
 }
 
@@ -129,7 +133,7 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
     long long most = 1;
     for (int l = 0; l < p.L; ++l)
       for (int sub = 0; sub < 4; ++sub) {
-        const long long t = large_sub_tasks(p, l, sub, factor ? 1 : 0, rhs ? a.d : 0, esz);
+        const long long t = large_sub_tasks(p, l, sub, factor ? 1 : 0, rhs ? a.d : 0, esz, h->tf32);
         if (t > most) most = t;
       }
     h->launches += 1;
@@ -142,14 +146,15 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < p.L && e == cudaSuccess; ++l)
     for (int sub = factor ? 0 : 1; sub < 3 && e == cudaSuccess; ++sub) {
-      e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz)), h->smem, h->stream);
+      e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz, h->tf32)), h->smem,
+                              h->stream);
       h->launches += 1;
     }
   if (e == cudaSuccess) e = launch_large_top<T>(b, f, h->smem, h->stream);
   h->launches += 1;
   if (rhs)
     for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
-      e = launch_large_sub<T>(b, l, 3, 0, grid_for(h, large_sub_tasks(p, l, 3, 0, b.d, esz)), h->smem, h->stream);
+      e = launch_large_sub<T>(b, l, 3, 0, grid_for(h, large_sub_tasks(p, l, 3, 0, b.d, esz, 0)), h->smem, h->stream);
       h->launches += 1;
     }
   return e;
@@ -209,6 +214,7 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->Ld);
   cudaFree(h->Wb);
   cudaFree(h->Eb);
+  cudaFree(h->d_tmap);
   cudaFree(h->Ltop);
   cudaFree(h->Y32);
   cudaFree(h->R32);
@@ -265,6 +271,14 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
   ok = ok && cudaMalloc((void **)&h->partial, kLogdetGrid * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&h->dst, sizeof(DevStatus)) == cudaSuccess;
   ok = ok && cudaMallocHost((void **)&h->hst, sizeof(DevStatus)) == cudaSuccess;
+  if (ok && h->large && prec == BDSS_TF32_IR && n % 4 == 0) {
+    // tensor-core Schur tiles read W^T rows of Wb through TMA
+    CUtensorMap map;
+    cudaError_t em = make_w_tensor_map(&map, (const float *)h->Wb, (long long)slots * n, n);
+    ok = em == cudaSuccess && cudaMalloc((void **)&h->d_tmap, sizeof(CUtensorMap)) == cudaSuccess &&
+         cudaMemcpy(h->d_tmap, &map, sizeof(CUtensorMap), cudaMemcpyHostToDevice) == cudaSuccess;
+    h->tf32 = ok ? 1 : 0;
+  }
   if (ok && is_mixed(h)) {
     const size_t nd = (size_t)N * n * d_max;
     ok = cudaMalloc((void **)&h->Y32, nd * sizeof(float)) == cudaSuccess;
@@ -510,6 +524,14 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e);
   return BDSS_OK;
+}
+
+bdss_status bdss_tc_selftest(double *max_rel_err) {
+  if (!max_rel_err) return BDSS_ERR_INVALID_ARG;
+  int st = 0;
+  cudaError_t e = run_tc_selftest(max_rel_err, &st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return (bdss_status)st;
 }
 
 const char *bdss_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda_error); }

@@ -20,6 +20,7 @@
 //                          slot j   <- W_R^T = (L_j^{-1} A_{j+1,j}^T)^T.
 //   Y    : N x n x d right-hand side / solution in T.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,6 +69,8 @@ struct Args {
   DevStatus *st;
   long long timeout_ns;
   int skip_barrier;      // test hook: 1-based barrier index CTA 0 skips
+  int tf32;              // large FP32 path: Schur products on tcgen05 (3xTF32)
+  const CUtensorMap *tmap_w;  // TMA map of Wb as (slots * n) rows x n FP32 columns
 };
 
 // Odd row stride of a staged n x n block (shared-memory bank spread).

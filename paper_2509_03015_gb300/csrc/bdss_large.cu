@@ -12,7 +12,7 @@ namespace bdss {
 enum { kSubA1 = 0, kSubA2 = 1, kSubB = 2, kSubC = 3 };
 
 template <typename T>
-__device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem, int *s_flag) {
+__device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem, int *s_flag, TcState *tc) {
   const int n = a.p.n, d = a.d;
   const long long Nl = a.p.Nl[l];
   const long long nE = Nl / 2, nS = (Nl + 1) / 2;
@@ -28,6 +28,22 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
       if (v * VT < largeA2_vectors(a, l, j, factor)) largeA2(a, l, j, v, factor, smem);
     }
   } else if (sub == kSubB) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc && factor) {
+        // D and E tiles on the tensor cores, RHS tiles on CUDA cores
+        const int nTC = largeB_tc_tiles(n), nR = largeB_tiles(n, false, d), nTB = nTC + nR;
+        for (long long t = blockIdx.x; t < nS * nTB; t += gridDim.x) {
+          const long long k = t / nTB;
+          const int u = (int)(t % nTB);
+          if (u < nTC) {
+            if (!largeB_tc(a, l, k, u, *tc)) return false;
+          } else {
+            largeB(a, l, k, u - nTC, false, smem);
+          }
+        }
+        return true;
+      }
+    }
     const int nTB = largeB_tiles(n, factor, d);
     for (long long t = blockIdx.x; t < nS * nTB; t += gridDim.x) largeB(a, l, t / nTB, (int)(t % nTB), factor, smem);
   } else {
@@ -37,29 +53,43 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_large_persistent(const __grid_constant__ Args<T> a, int factor,
-                                                               int rhs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_flag;
+__device__ void large_body(const Args<T> &a, int factor, int rhs, unsigned char *smem_raw, int *s_flag,
+                           TcState *tc) {
   T *smem = reinterpret_cast<T *>(smem_raw);
   int bar = 0;
   for (int l = 0; l < a.p.L; ++l) {
     if (factor) {
-      large_sub(a, l, kSubA1, true, smem, &s_flag);
+      large_sub(a, l, kSubA1, true, smem, s_flag, tc);
       if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
     }
-    large_sub(a, l, kSubA2, factor != 0, smem, &s_flag);
+    large_sub(a, l, kSubA2, factor != 0, smem, s_flag, tc);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
-    large_sub(a, l, kSubB, factor != 0, smem, &s_flag);
+    large_sub(a, l, kSubB, factor != 0, smem, s_flag, tc);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
-  if (blockIdx.x == 0) largeTop(a, factor != 0, reinterpret_cast<double *>(smem_raw), &s_flag);
+  if (blockIdx.x == 0) largeTop(a, factor != 0, reinterpret_cast<double *>(smem_raw), s_flag);
   if (!rhs || a.p.L == 0) return;
   if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   for (int l = a.p.L - 1; l >= 0; --l) {
-    large_sub(a, l, kSubC, false, smem, &s_flag);
+    large_sub(a, l, kSubC, false, smem, s_flag, tc);
     if (l > 0 && !grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
+}
+
+// The tensor-core state (TMEM, mbarriers) is set up once per CTA when the
+// TF32 mode is on and released on every way out of the kernel body.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_large_persistent(const __grid_constant__ Args<T> a, int factor,
+                                                               int rhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_flag;
+  __shared__ uint64_t s_bars[2];
+  __shared__ uint32_t s_tmem;
+  TcState tc;
+  const bool use_tc = std::is_same<T, float>::value && a.tf32 && factor;
+  if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
+  large_body(a, factor, rhs, smem_raw, &s_flag, use_tc ? &tc : nullptr);
+  if (use_tc) tc_end(tc);
 }
 
 template <typename T>
@@ -67,8 +97,14 @@ __global__ void __launch_bounds__(kThreads) k_large_sub(const __grid_constant__ 
                                                         int factor) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_flag;
+  __shared__ uint64_t s_bars[2];
+  __shared__ uint32_t s_tmem;
   if (ld_relaxed_i32(&a.st->status) != 0) return;
-  large_sub(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag);
+  TcState tc;
+  const bool use_tc = std::is_same<T, float>::value && a.tf32 && factor && sub == kSubB;
+  if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
+  large_sub(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, use_tc ? &tc : nullptr);
+  if (use_tc) tc_end(tc);
 }
 
 template <typename T>
@@ -148,12 +184,16 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
   }
 }
 
+__global__ void k_tc_selftest(const __grid_constant__ CUtensorMap map, const float *W, int n, double *err,
+                              int *status, long long timeout_ns);
+
 // ---------------------------------------------------------------------------
 template <typename T>
 size_t smem_bytes_large(int n, int d) {
   size_t b = smem_large(n, d, (int)sizeof(T)) * sizeof(T);
   const size_t top = smem_large_top(n, d) * sizeof(double);
   if (top > b) b = top;
+  if (sizeof(T) == 4 && kTcSmemBytes > b) b = kTcSmemBytes;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -163,7 +203,8 @@ cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const void *kernels[] = {(const void *)k_large_persistent<T>, (const void *)k_large_sub<T>,
-                           (const void *)k_large_top<T>, (const void *)k_residual_rows};
+                           (const void *)k_large_top<T>, (const void *)k_residual_rows,
+                           (const void *)k_tc_selftest};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -201,14 +242,123 @@ cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStre
   return cudaGetLastError();
 }
 
-long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz) {
+long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32) {
   const long long Nl = p.Nl[l], nE = Nl / 2, nS = (Nl + 1) / 2;
   if (sub == kSubA1 || sub == kSubC) return nE;
   if (sub == kSubA2) {
     const int VT = vec_tile(esz);
     return nE * (((factor ? 2 * p.n : 0) + d + VT - 1) / VT);
   }
+  if (tf32 && factor) return nS * (largeB_tc_tiles(p.n) + largeB_tiles(p.n, false, d));
   return nS * largeB_tiles(p.n, factor != 0, d);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor map of the coupling buffer for the TMA loads of the TF32 tiles.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows, int n) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = (EncodeTiledFn)p;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)Wb, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Self-check of the tensor-core tile: one 128 x 128 tile C = A B^T, K = 256,
+// 3xTF32 on tcgen05 against an FP64 CUDA-core product of the same FP32
+// inputs.  err[0] = max |C_tc - C_ref| / max(sum_k |a||b|).
+__global__ void __launch_bounds__(kThreads) k_tc_selftest(const __grid_constant__ CUtensorMap map, const float *W,
+                                                          int n, double *err, int *status, long long timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t s_bars[2];
+  __shared__ uint32_t s_tmem;
+  TcState tc;
+  tc_begin(tc, smem_raw, s_bars, &s_tmem);
+  // rows 0..127 (A) against rows 128..255 (B) of the n x n matrix W
+  const bool ok = tc_accumulate(tc, &map, 0, 128, n, true, timeout_ns);
+  if (!ok) {
+    if (threadIdx.x == 0) *status = kStTimeout;
+  } else {
+    float v[64];
+    int row, col0;
+    tc_read_row(tc, v, row, col0);
+    double worst = 0.0;
+    for (int j = 0; j < 64; ++j) {
+      const int c = col0 + j;
+      double ref = 0.0, mag = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double x = W[(size_t)row * n + k], y = W[(size_t)(128 + c) * n + k];
+        ref = fma(x, y, ref);
+        mag += fabs(x * y);
+      }
+      const double e = fabs((double)v[j] - ref) / (mag > 0 ? mag : 1.0);
+      worst = e > worst ? e : worst;
+    }
+    atomicMax(reinterpret_cast<unsigned long long *>(err), (unsigned long long)__double_as_longlong(worst));
+  }
+  tc_end(tc);
+}
+
+cudaError_t run_tc_selftest(double *max_err, int *status) {
+  const int n = 256;
+  float *W = nullptr;
+  double *d_err = nullptr;
+  int *d_status = nullptr;
+  cudaError_t e = cudaMalloc(&W, (size_t)n * n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int));
+  float *h = nullptr;
+  if (e == cudaSuccess) h = (float *)malloc((size_t)n * n * sizeof(float));
+  if (e == cudaSuccess && h) {
+    unsigned s = 12345u;
+    for (int i = 0; i < n * n; ++i) {  // deterministic values in (-1, 1), full FP32 mantissas
+      s = s * 1664525u + 1013904223u;
+      h[i] = (float)((double)(s >> 8) / (double)(1u << 24) * 2.0 - 1.0);
+    }
+    e = cudaMemcpy(W, h, (size_t)n * n * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  free(h);
+  CUtensorMap map;
+  if (e == cudaSuccess) e = make_w_tensor_map(&map, W, n, n);
+  if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void *)k_tc_selftest);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void *)k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+  }
+  if (e == cudaSuccess) {
+    k_tc_selftest<<<1, kThreads, kTcSmemBytes>>>(map, W, n, d_err, d_status, 2000000000LL);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(max_err, d_err, sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(W);
+  cudaFree(d_err);
+  cudaFree(d_status);
+  return e;
 }
 
 cudaError_t launch_residual_rows(long long N, int n, int d, const double *A_diag, const double *A_sub,

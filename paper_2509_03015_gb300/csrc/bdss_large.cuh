@@ -13,7 +13,10 @@
 //       (Algorithms 6, 2), blocked from the bottom tile up;
 //   top the remaining block, FP64, blocked, in Ltop.
 #pragma once
+#include <type_traits>
+
 #include "bdss_device.cuh"
+#include "bdss_tc.cuh"
 
 namespace bdss {
 
@@ -429,6 +432,80 @@ __device__ void largeB(const Args<T> &a, int l, long long k, int t, bool factor,
     }
   }
   __syncthreads();
+}
+
+// Tensor-core tiles of a separator's Schur update (large FP32 path, TF32
+// mode): 128 x 128 output tiles, lower D tiles then E tiles.
+__host__ __device__ inline int largeB_tc_tiles(int n) {
+  const int t = (n + kTcM - 1) / kTcM;
+  return t * (t + 1) / 2 + t * t;
+}
+
+// Tile t of separator s = 2k at level l on tcgen05 (3xTF32).  Returns false on
+// a timed-out wait (the status word is then set).
+__device__ inline bool largeB_tc(const Args<float> &a, int l, long long k, int t, TcState &tc) {
+  const int n = a.p.n, nt = (n + kTcM - 1) / kTcM, nD = nt * (nt + 1) / 2;
+  const long long Nl = a.p.Nl[l];
+  const long long s = 2 * k;
+  const bool hasM = (s >= 2), hasP = (s + 1 < Nl), hasE = (s + 2 < Nl);
+  const long long orig = s << l;
+  const size_t nn = (size_t)n * n;
+  const long long slot0 = a.p.off[l];
+  bool ok = true;
+  int ti, tj;
+  if (t < nD) {
+    ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    tj = t - ti * (ti + 1) / 2;
+    bool first = true;
+    if (hasM) {
+      const int base = (int)((slot0 + s - 1) * n);
+      ok = tc_accumulate(tc, a.tmap_w, base + ti * kTcM, base + tj * kTcM, n, first, a.timeout_ns);
+      first = false;
+    }
+    if (ok && hasP) {
+      const int base = (int)((slot0 + s) * n);
+      ok = tc_accumulate(tc, a.tmap_w, base + ti * kTcM, base + tj * kTcM, n, first, a.timeout_ns);
+    }
+  } else {
+    if (!hasE) return true;
+    const int u = t - nD;
+    ti = u / nt;
+    tj = u - ti * nt;
+    ok = tc_accumulate(tc, a.tmap_w, (int)((slot0 + s + 1) * n) + ti * kTcM, (int)((slot0 + s) * n) + tj * kTcM, n,
+                       true, a.timeout_ns);
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) set_status(a.st, kStTimeout, l, orig);
+    return false;
+  }
+  float v[64];
+  int row, col0;
+  tc_read_row(tc, v, row, col0);
+  const int R = ti * kTcM + row;
+  if (t < nD) {
+    float *Dg = a.Ld + (size_t)orig * nn;
+    const double *Ag = a.A_diag + (size_t)orig * nn;
+    if (R < n)
+      for (int j = 0; j < 64; ++j) {
+        const int C = tj * kTcN + col0 + j;
+        if (C <= R && C < n) {
+          const float base = (l == 0) ? 0.5f * ((float)ldcg(Ag + (size_t)R * n + C) + (float)ldcg(Ag + (size_t)C * n + R))
+                                      : ldcg(Dg + (size_t)R * n + C);
+          Dg[(size_t)R * n + C] = base - v[j];
+        }
+      }
+  } else {
+    float *En = a.Eb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
+    if (R < n)
+      for (int j = 0; j < 64; ++j) {
+        const int C = tj * kTcN + col0 + j;
+        if (C < n) En[(size_t)R * n + C] = -v[j];
+      }
+  }
+  tc_fence_before();
+  __syncthreads();
+  return true;
 }
 
 // C: downward pass for eliminated position j of level l.
