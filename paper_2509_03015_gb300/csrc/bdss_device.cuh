@@ -186,33 +186,162 @@ __device__ void stage_cols(T *s, int ld, const S *g, int n, int m) {
   }
 }
 
-// Cholesky-Crout of the staged lower triangle (Algorithm 1, potrf), in
-// place: row i is handled by thread i; two barriers per column.  On exit the
-// diagonal holds 1 / L_kk.  Returns the first failing column + 1, or 0.
+// Map a lower-triangle linear index t to (a, b), 0 <= b <= a.
+__device__ __forceinline__ void tri_index(int t, int &a, int &b) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  while (r * (r + 1) / 2 > t) --r;
+  a = r;
+  b = t - r * (r + 1) / 2;
+}
+
+// 1/sqrt(x) for x > 0.  FP64: an FP32 seed (x inside the FP32 range)
+// refined by two Newton-Raphson steps on f(y) = 1/y^2 - x, i.e.
+// y <- y (3/2 - (x/2) y^2); each step roughly doubles the correct bits
+// (23 -> 46 -> full precision).  About 7 FP64 instructions instead of a
+// square root and a division on the narrow FP64 pipe.  FP32: rsqrtf.
+__device__ __forceinline__ float rsqrt_nr(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+// Cholesky of the staged lower triangle (Algorithm 1, potrf), in place,
+// right-looking: per column, warp 0 takes the pivot and scales the column,
+// then every thread updates the trailing lower triangle, so the FP64 work
+// of the update runs in whole warps.  On exit the diagonal holds 1 / L_kk.
+// Returns the first failing column + 1, or 0.
 template <typename T>
 __device__ int chol_staged(T *s, int ld, int n, int *s_flag) {
-  const int i = threadIdx.x;
-  if (i == 0) *s_flag = 0;
-  __syncthreads();
+  const int tid = threadIdx.x;
+  if (tid == 0) *s_flag = 0;
   for (int k = 0; k < n; ++k) {
-    T acc = T(0);
-    if (i >= k && i < n) {
-      acc = s[i * ld + k];
-      const T *ri = s + i * ld;
-      const T *rk = s + k * ld;
-      for (int p = 0; p < k; ++p) acc = fma(-ri[p], rk[p], acc);
-      if (i == k) {
-        const bool ok = (acc > T(0)) && isfinite(acc);
-        const T l = ok ? sqrt(acc) : T(1);
-        s[k * ld + k] = T(1) / l;
+    __syncthreads();
+    if (tid < 32) {
+      const T dkk = s[k * ld + k];
+      const bool ok = (dkk > T(0)) && isfinite(dkk);
+      const T r = rsqrt_nr(ok ? dkk : T(1));
+      for (int i = k + 1 + tid; i < n; i += 32) s[i * ld + k] *= r;
+      __syncwarp();
+      if (tid == 0) {
+        s[k * ld + k] = r;
         if (!ok && *s_flag == 0) *s_flag = k + 1;
       }
     }
     __syncthreads();
-    if (i > k && i < n) s[i * ld + k] = acc * s[k * ld + k];
-    __syncthreads();
+    if (*s_flag) break;
+    const int m = n - k - 1;
+    const int cnt = m * (m + 1) / 2;
+    for (int t = tid; t < cnt; t += blockDim.x) {
+      int a, b;
+      tri_index(t, a, b);
+      const int i = k + 1 + a, j = k + 1 + b;
+      s[i * ld + j] = fma(-s[i * ld + k], s[j * ld + k], s[i * ld + j]);
+    }
   }
+  __syncthreads();
   return *s_flag;
+}
+
+// Warp-cooperative substitutions for a few right-hand sides (n <= 64): lane
+// l owns rows l and l + 32 of every vector (vectors are rows of V, stride
+// ld); each pivot is finished by its owning lane and broadcast by shuffle,
+// then all lanes update their rows.  One warp runs the whole solve, so the
+// FP64 work of a handful of vectors fills its lanes instead of one lane per
+// vector.  Call from exactly one warp.
+template <typename T>
+__device__ void trsv_fwd_warp(const T *sL, int ld, int n, T *V, int nv) {
+  constexpr int C = 4;
+  const int lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < nv; c0 += C) {
+    const int cn = min(C, nv - c0);
+    T y0[C], y1[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      y0[c] = (c < cn && lane < n) ? V[(c0 + c) * ld + lane] : T(0);
+      y1[c] = (c < cn && lane + 32 < n) ? V[(c0 + c) * ld + lane + 32] : T(0);
+    }
+    for (int r = 0; r < n; ++r) {
+      const T rd = sL[r * ld + r];
+      const int owner = r & 31;
+      T yr[C];
+      if (r < 32) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) yr[c] = __shfl_sync(0xffffffffu, y0[c] * rd, owner);
+        if (lane == owner)
+#pragma unroll
+          for (int c = 0; c < C; ++c) y0[c] = yr[c];
+        const T l0 = (lane > r && lane < n) ? sL[lane * ld + r] : T(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) y0[c] = fma(-l0, yr[c], y0[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) yr[c] = __shfl_sync(0xffffffffu, y1[c] * rd, owner);
+        if (lane == owner)
+#pragma unroll
+          for (int c = 0; c < C; ++c) y1[c] = yr[c];
+      }
+      if (n > 32) {
+        const T l1 = (lane + 32 > r && lane + 32 < n) ? sL[(lane + 32) * ld + r] : T(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) y1[c] = fma(-l1, yr[c], y1[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      if (c < cn && lane < n) V[(c0 + c) * ld + lane] = y0[c];
+      if (c < cn && lane + 32 < n) V[(c0 + c) * ld + lane + 32] = y1[c];
+    }
+  }
+}
+
+// L^T z = t, same organisation, from the last row up.
+template <typename T>
+__device__ void trsv_bwd_warp(const T *sL, int ld, int n, T *V, int nv) {
+  constexpr int C = 4;
+  const int lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < nv; c0 += C) {
+    const int cn = min(C, nv - c0);
+    T y0[C], y1[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      y0[c] = (c < cn && lane < n) ? V[(c0 + c) * ld + lane] : T(0);
+      y1[c] = (c < cn && lane + 32 < n) ? V[(c0 + c) * ld + lane + 32] : T(0);
+    }
+    for (int r = n - 1; r >= 0; --r) {
+      const T rd = sL[r * ld + r];
+      const int owner = r & 31;
+      T zr[C];
+      if (r >= 32) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) zr[c] = __shfl_sync(0xffffffffu, y1[c] * rd, owner);
+        if (lane == owner)
+#pragma unroll
+          for (int c = 0; c < C; ++c) y1[c] = zr[c];
+        const T l1 = (lane + 32 < r) ? sL[r * ld + lane + 32] : T(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) y1[c] = fma(-l1, zr[c], y1[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) zr[c] = __shfl_sync(0xffffffffu, y0[c] * rd, owner);
+        if (lane == owner)
+#pragma unroll
+          for (int c = 0; c < C; ++c) y0[c] = zr[c];
+      }
+      const T l0 = (lane < r) ? sL[r * ld + lane] : T(0);
+#pragma unroll
+      for (int c = 0; c < C; ++c) y0[c] = fma(-l0, zr[c], y0[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      if (c < cn && lane < n) V[(c0 + c) * ld + lane] = y0[c];
+      if (c < cn && lane + 32 < n) V[(c0 + c) * ld + lane + 32] = y1[c];
+    }
+  }
 }
 
 // Forward substitution L w = v for `nv` staged vectors (rows of V, stride
@@ -243,14 +372,6 @@ __device__ void trsv_bwd_rows(const T *sL, int ld, int n, T *V, int nv) {
   }
 }
 
-// Map a lower-triangle linear index t to (a, b), 0 <= b <= a.
-__device__ __forceinline__ void tri_index(int t, int &a, int &b) {
-  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while ((r + 1) * (r + 2) / 2 <= t) ++r;
-  while (r * (r + 1) / 2 > t) --r;
-  a = r;
-  b = t - r * (r + 1) / 2;
-}
 
 // Shared-memory words (in T) of each phase.
 __host__ __device__ inline size_t smem_phaseA(int n, int d) {
@@ -323,20 +444,20 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       if (c <= r) Lg[e] = sL[r * ld + c];
     }
   }
-  // forward substitution on the staged coupling vectors and the RHS vectors
+  // forward substitution: one coupling vector per thread; the RHS vectors by
+  // one warp (warp-cooperative), concurrently when a warp is free
   {
-    const int rhs0 = factor ? 2 * n : 0;  // first RHS row of sV
-    for (int v = threadIdx.x; v < nW + d; v += blockDim.x) {
-      T *w = sV + (size_t)(v < nW ? v : rhs0 + (v - nW)) * ld;
-      for (int r = 0; r < n; ++r) {
-        T acc = w[r];
-        const T *lr = sL + r * ld;
-        for (int p = 0; p < r; ++p) acc = fma(-lr[p], w[p], acc);
-        w[r] = acc * lr[r];
-      }
+    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    const int wc = (nW + 31) >> 5;
+    const bool side = (nW <= (int)blockDim.x) && (wc < nwarps);
+    trsv_fwd_rows(sL, ld, n, sV, nW);
+    if (d > 0 && side && warp == wc) trsv_fwd_warp(sL, ld, n, sB, d);
+    __syncthreads();
+    if (d > 0 && !side) {
+      if (warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
+      __syncthreads();
     }
   }
-  __syncthreads();
   if (factor) {
     T *W = a.Wb + (size_t)a.p.off[l] * nn;
     T *WL = W + (size_t)(j - 1) * nn;
@@ -477,9 +598,11 @@ __device__ bool top_block(const Args<T> &a, bool factor, double *smem, int *s_fl
     }
   }
   if (d > 0) {
-    trsv_fwd_rows(sL, ld, n, sB, d);
-    __syncthreads();
-    trsv_bwd_rows(sL, ld, n, sB, d);
+    if (threadIdx.x < 32) {
+      trsv_fwd_warp(sL, ld, n, sB, d);
+      __syncwarp();
+      trsv_bwd_warp(sL, ld, n, sB, d);
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
       const int i = e / d, c = e - i * d;
@@ -528,7 +651,7 @@ __device__ void phaseC(const Args<T> &a, int l, long long j, T *smem) {
     sT[c * ld + q] = acc;
   }
   __syncthreads();
-  trsv_bwd_rows(sL, ld, n, sT, d);
+  if (threadIdx.x < 32) trsv_bwd_warp(sL, ld, n, sT, d);
   __syncthreads();
   T *Yo = a.Y + (size_t)orig * nd;
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
