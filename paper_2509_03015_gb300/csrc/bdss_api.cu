@@ -137,7 +137,7 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
         if (t > most) most = t;
       }
     h->launches += 1;
-    h->barriers += (factor ? 3 : 2) * p.L + ((rhs && p.L > 0) ? p.L : 0);
+    h->barriers += 1 + (factor ? 3 : 2) * p.L + ((rhs && p.L > 0) ? p.L : 0);
     return launch_large_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid_for(h, most), h->smem, h->stream);
   }
   Args<T> b = a;
@@ -167,7 +167,7 @@ static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool r
   if (h->persistent) {
     const int grid = grid_for(h, (p.N + 1) / 2);
     h->launches += 1;
-    int bars = 2 * p.L;
+    int bars = 1 + 2 * p.L;  // the spread-rank barrier, then two per level
     if (rhs && p.L > 0) bars += 1 + (p.L - 1);
     h->barriers += bars;
     return launch_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid, h->smem, h->stream);

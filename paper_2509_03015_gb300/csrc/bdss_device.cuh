@@ -32,6 +32,9 @@ constexpr int kMaxN = 64;
 
 enum { kStOk = 0, kStNotSPD = 2, kStTimeout = 6 };
 
+constexpr int kSmSlots = 256;  // SM-id table of the spread rank
+constexpr int kCtaSlots = 8;   // co-resident CTA classes per SM
+
 struct DevStatus {
   unsigned int bar_count;  // arrivals at the current grid barrier
   unsigned int bar_gen;    // generation of the grid barrier
@@ -40,6 +43,8 @@ struct DevStatus {
   long long level;         // NOT_SPD: level and original block of the pivot
   long long block;
   unsigned long long nrm[4];  // residual kernel: bit patterns of max-norms (>= 0)
+  unsigned int sm_count[kSmSlots];    // CTAs seen per SM (spread rank)
+  unsigned int slot_count[kCtaSlots]; // CTAs per arrival slot (spread rank)
 };
 
 struct Plan {
@@ -147,6 +152,35 @@ static __device__ __noinline__ bool grid_barrier(DevStatus *st, long long timeou
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Dense rank of this CTA in a cooperative grid such that ranks 0..S-1 sit on
+// S different SMs, S..2S-1 again on different SMs, and so on (S = SMs in
+// use): each CTA takes an arrival slot on its SM, then an index within its
+// slot class; after one grid barrier the class sizes are final and
+// rank = (CTAs of lower classes) + index.  Work loops that stride by this
+// rank keep a level with fewer blocks than SMs on distinct SMs (consecutive
+// block indices of a launch may share an SM).  Returns -1 if the barrier
+// reports an error.
+static __device__ __noinline__ int spread_rank(DevStatus *st, long long timeout_ns) {
+  __shared__ int s_rank;
+  __shared__ unsigned s_slot, s_idx;
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const unsigned slot = atomicAdd(&st->sm_count[smid % kSmSlots], 1u);
+    const unsigned cls = slot < kCtaSlots ? slot : kCtaSlots - 1;
+    s_slot = cls;
+    s_idx = atomicAdd(&st->slot_count[cls], 1u);
+  }
+  if (!grid_barrier(st, timeout_ns, 0, -1)) return -1;
+  if (threadIdx.x == 0) {
+    unsigned prefix = 0;
+    for (unsigned c = 0; c < s_slot; ++c) prefix += ld_acquire_u32(&st->slot_count[c]);
+    s_rank = (int)(prefix + s_idx);
+  }
+  __syncthreads();
+  return s_rank;
 }
 
 // ---------------------------------------------------------------------------
@@ -345,17 +379,47 @@ __device__ void trsv_bwd_warp(const T *sL, int ld, int n, T *V, int nv) {
 }
 
 // Forward substitution L w = v for `nv` staged vectors (rows of V, stride
-// ld), one vector per thread; L staged with reciprocal diagonal.
+// ld); L staged with reciprocal diagonal.  On this GPU one warp issues at
+// most one FP64 instruction per ~64 cycles and the SM's FP64 pipe needs
+// four or more warps to be full, so the work is spread over all warps: rows
+// are taken 8 at a time; the update of a row block from the rows already
+// solved runs over (vector, row) pairs on every thread, then one thread per
+// vector solves the 8 x 8 diagonal triangle.  Same FP64 operation count as
+// the row-by-row sweep.  All threads of the CTA must call it.
 template <typename T>
 __device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    T *w = V + v * ld;
-    for (int r = 0; r < n; ++r) {
-      T acc = w[r];
-      const T *lr = sL + r * ld;
-      for (int p = 0; p < r; ++p) acc = fma(-lr[p], w[p], acc);
-      w[r] = acc * lr[r];
+  constexpr int RB = 8;
+  for (int r0 = 0; r0 < n; r0 += RB) {
+    const int rb = min(RB, n - r0);
+    if (r0 > 0) {
+      for (int t = threadIdx.x; t < nv * rb; t += blockDim.x) {
+        const int i = t / nv, v = t - i * nv;
+        T *w = V + v * ld;
+        const T *lr = sL + (r0 + i) * ld;
+        T acc = w[r0 + i];
+        for (int p = 0; p < r0; ++p) acc = fma(-lr[p], w[p], acc);
+        w[r0 + i] = acc;
+      }
+      __syncthreads();
     }
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      T *w = V + v * ld + r0;
+      T acc[RB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) acc[i] = (i < rb) ? w[i] : T(0);
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        if (i < rb) {
+          T a = acc[i];
+#pragma unroll
+          for (int q = 0; q < i; ++q) a = fma(-sL[(r0 + i) * ld + r0 + q], acc[q], a);
+          acc[i] = a * sL[(r0 + i) * ld + r0 + i];
+        }
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        if (i < rb) w[i] = acc[i];
+    }
+    __syncthreads();
   }
 }
 
@@ -374,13 +438,17 @@ __device__ void trsv_bwd_rows(const T *sL, int ld, int n, T *V, int nv) {
 
 
 // Shared-memory words (in T) of each phase.
+// Phase A holds L, one pass of n coupling vectors and the d RHS vectors;
+// phase B holds two W^T blocks and two d-vector sets.  (Two passes / two
+// stages keep a CTA near 70 KB at n = 64 in FP64, so that three CTAs share
+// an SM.)
 __host__ __device__ inline size_t smem_phaseA(int n, int d) {
   const int ld = ldstride(n);
-  return (size_t)n * ld + (size_t)(2 * n + d) * ld + 8;
+  return (size_t)(2 * n + d) * ld + 8;
 }
 __host__ __device__ inline size_t smem_phaseB(int n, int d) {
   const int ld = ldstride(n);
-  return (size_t)3 * n * ld + (size_t)2 * d * ld + 8;
+  return (size_t)(2 * n + 2 * d) * ld + 8;
 }
 __host__ __device__ inline size_t smem_down(int n, int d) {
   const int ld = ldstride(n);
@@ -405,22 +473,18 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
   const long long orig = j << l;
   const size_t nn = (size_t)n * n;
   T *sL = smem;
-  T *sV = sL + n * ld;
-  const int nW = factor ? (hasR ? 2 * n : n) : 0;  // coupling vectors
-  T *sB = sV + (size_t)(factor ? 2 * n : 0) * ld;   // RHS vectors
+  T *sV = sL + (size_t)n * ld;                         // n coupling vectors (one pass)
+  T *sB = sV + (size_t)(factor ? n : 0) * ld;           // d RHS vectors
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const T *E = (l == 0) ? nullptr : a.Wb + (size_t)a.p.off[l] * nn;
+  T *W = a.Wb + (size_t)a.p.off[l] * nn;
 
   if (factor) {
     if (l == 0) stage_sym_lower(sL, ld, a.A_diag + orig * nn, n);
     else stage_lower(sL, ld, a.Ld + orig * nn, n);
-    // couplings: E_l[j-1] = A_{j,j-1} (columns), E_l[j] = A_{j+1,j} (rows)
-    if (l == 0) {
-      stage_cols(sV, ld, a.A_sub + (size_t)(j - 1) * nn, n, n);
-      if (hasR) stage_rows(sV + (size_t)n * ld, ld, a.A_sub + (size_t)j * nn, n);
-    } else {
-      const T *E = a.Wb + (size_t)a.p.off[l] * nn;
-      stage_cols(sV, ld, E + (size_t)(j - 1) * nn, n, n);
-      if (hasR) stage_rows(sV + (size_t)n * ld, ld, E + (size_t)j * nn, n);
-    }
+    // pass 1 vectors: the columns of E_l[j-1] = A_{j,j-1}
+    if (l == 0) stage_cols(sV, ld, a.A_sub + (size_t)(j - 1) * nn, n, n);
+    else stage_cols(sV, ld, E + (size_t)(j - 1) * nn, n, n);
   } else {
     stage_lower(sL, ld, a.Ld + orig * nn, n);
   }
@@ -444,33 +508,19 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       if (c <= r) Lg[e] = sL[r * ld + c];
     }
   }
-  // forward substitution: one coupling vector per thread; the RHS vectors by
-  // one warp (warp-cooperative), concurrently when a warp is free
-  {
-    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
-    const int wc = (nW + 31) >> 5;
-    const bool side = (nW <= (int)blockDim.x) && (wc < nwarps);
-    trsv_fwd_rows(sL, ld, n, sV, nW);
-    if (d > 0 && side && warp == wc) trsv_fwd_warp(sL, ld, n, sB, d);
+  // pass 1: W_L over all warps, then the RHS vectors by one warp
+  // (warp-cooperative)
+  if (factor) trsv_fwd_rows(sL, ld, n, sV, n);
+  if (d > 0) {
+    if (warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
     __syncthreads();
-    if (d > 0 && !side) {
-      if (warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
-      __syncthreads();
-    }
   }
+  (void)nwarps;
   if (factor) {
-    T *W = a.Wb + (size_t)a.p.off[l] * nn;
     T *WL = W + (size_t)(j - 1) * nn;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int c = e / n, i = e - c * n;
       WL[e] = sV[c * ld + i];
-    }
-    if (hasR) {
-      T *WR = W + (size_t)j * nn;
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int c = e / n, i = e - c * n;
-        WR[e] = sV[(n + c) * ld + i];
-      }
     }
   }
   if (d > 0) {
@@ -478,6 +528,20 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
     for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
       const int i = e / d, c = e - i * d;
       Yj[e] = sB[c * ld + i];
+    }
+  }
+  if (factor && hasR) {
+    // pass 2: W_R from the rows of E_l[j] = A_{j+1,j}
+    __syncthreads();
+    if (l == 0) stage_rows(sV, ld, a.A_sub + (size_t)j * nn, n);
+    else stage_rows(sV, ld, E + (size_t)j * nn, n);
+    __syncthreads();
+    trsv_fwd_rows(sL, ld, n, sV, n);
+    __syncthreads();
+    T *WR = W + (size_t)j * nn;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int c = e / n, i = e - c * n;
+      WR[e] = sV[c * ld + i];
     }
   }
   __syncthreads();
@@ -488,8 +552,9 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
 // Phase B: separator position s = 2k of level l (Algorithm 3 + Assemble,
 // Algorithm 5's separator update):
 //   S_ss      = D_s - W_R(s-1)^T W_R(s-1) - W_L(s+1)^T W_L(s+1)  (lower)
-//   S_{s+2,s} = -W_R(s+1)^T W_L(s+1)  -> region l+1, slot k
 //   b_s      -= W_R(s-1)^T y_{s-1} + W_L(s+1)^T y_{s+1}
+//   S_{s+2,s} = -W_R(s+1)^T W_L(s+1)  -> region l+1, slot k
+// W_R(s+1)^T is staged over W_R(s-1)^T once the first two are done.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *smem) {
@@ -499,14 +564,12 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
   const bool hasM = (s >= 2), hasP = (s + 1 < Nl), hasE = (s + 2 < Nl);
   const long long orig = s << l;
   const size_t nn = (size_t)n * n;
-  T *sW0 = smem;                      // W_R(s-1)^T
+  T *sW0 = smem;                      // W_R(s-1)^T, later W_R(s+1)^T
   T *sW1 = sW0 + (size_t)n * ld;      // W_L(s+1)^T
-  T *sW2 = sW1 + (size_t)n * ld;      // W_R(s+1)^T
-  T *sY = sW2 + (size_t)n * ld;       // y_{s-1}, y_{s+1} as d vectors each
+  T *sY = sW1 + (size_t)n * ld;       // y_{s-1}, y_{s+1} as d vectors each
   const T *W = a.Wb + (size_t)a.p.off[l] * nn;
   if (hasM) stage_rows(sW0, ld, W + (size_t)(s - 1) * nn, n);
   if (hasP) stage_rows(sW1, ld, W + (size_t)s * nn, n);
-  if (factor && hasE) stage_rows(sW2, ld, W + (size_t)(s + 1) * nn, n);
   if (d > 0) {
     if (hasM) stage_cols(sY, ld, a.Y + (size_t)((s - 1) << l) * n * d, n, d);
     if (hasP) stage_cols(sY + (size_t)d * ld, ld, a.Y + (size_t)((s + 1) << l) * n * d, n, d);
@@ -533,16 +596,6 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
       }
       Dg[r * n + c] = acc;
     }
-    if (hasE) {
-      T *En = a.Wb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int r = e / n, c = e - r * n;
-        const T *wr = sW2 + r * ld, *wc = sW1 + c * ld;
-        T acc = T(0);
-        for (int q = 0; q < n; ++q) acc = fma(-wr[q], wc[q], acc);
-        En[e] = acc;
-      }
-    }
   }
   if (d > 0) {
     const size_t boff = (size_t)orig * n * d;
@@ -561,6 +614,19 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
         for (int q = 0; q < n; ++q) acc = fma(-wr[q], y[q], acc);
       }
       a.Y[boff + e] = acc;
+    }
+  }
+  if (factor && hasE) {
+    __syncthreads();
+    stage_rows(sW0, ld, W + (size_t)(s + 1) * nn, n);
+    __syncthreads();
+    T *En = a.Wb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      const T *wr = sW0 + r * ld, *wc = sW1 + c * ld;
+      T acc = T(0);
+      for (int q = 0; q < n; ++q) acc = fma(-wr[q], wc[q], acc);
+      En[e] = acc;
     }
   }
   __syncthreads();
@@ -638,7 +704,7 @@ __device__ void phaseC(const Args<T> &a, int l, long long j, T *smem) {
   const T *WL = W + (size_t)(j - 1) * nn;   // W_L^T: WL[c][q] = W_L[q][c]
   const T *WR = W + (size_t)j * nn;
   const T *Yj = a.Y + (size_t)orig * nd;
-  // t[q][c] = y[q][c] - sum_a W_L[q][a] x_{j-1}[a][c] - sum_a W_R[q][a] x_{j+1}[a][c]
+  // t[q][c] = y[q][c] - sum_p W_L[q][p] x_{j-1}[p][c] - sum_p W_R[q][p] x_{j+1}[p][c]
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
     const int c = e / n, q = e - c * n;
     T acc = ldcg(Yj + (size_t)q * d + c);

@@ -13,28 +13,30 @@ namespace bdss {
 enum { kModeFactor = 1, kModeRhs = 2 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_persistent(const __grid_constant__ Args<T> a, int mode) {
+__global__ void __launch_bounds__(kThreads, 3) k_persistent(const __grid_constant__ Args<T> a, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_flag;
   T *smem = reinterpret_cast<T *>(smem_raw);
   const bool factor = (mode & kModeFactor) != 0;
   const bool rhs = (mode & kModeRhs) != 0 && a.d > 0;  // the host sets a.d = 0 without RHS
   int bar = 0;
+  const int rank = spread_rank(a.st, a.timeout_ns);
+  if (rank < 0) return;
   for (int l = 0; l < a.p.L; ++l) {
     const long long Nl = a.p.Nl[l];
     const long long nElim = Nl / 2, nSep = (Nl + 1) / 2;
-    for (long long m = blockIdx.x; m < nElim; m += gridDim.x)
+    for (long long m = rank; m < nElim; m += gridDim.x)
       if (!phaseA(a, l, 2 * m + 1, factor, smem, &s_flag)) break;
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
-    for (long long k = blockIdx.x; k < nSep; k += gridDim.x) phaseB(a, l, k, factor, smem);
+    for (long long k = rank; k < nSep; k += gridDim.x) phaseB(a, l, k, factor, smem);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
-  if (blockIdx.x == 0) top_block(a, factor, reinterpret_cast<double *>(smem_raw), &s_flag);
+  if (rank == 0) top_block(a, factor, reinterpret_cast<double *>(smem_raw), &s_flag);
   if (!rhs || a.p.L == 0) return;
   if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   for (int l = a.p.L - 1; l >= 0; --l) {
     const long long nElim = a.p.Nl[l] / 2;
-    for (long long m = blockIdx.x; m < nElim; m += gridDim.x) phaseC(a, l, 2 * m + 1, smem);
+    for (long long m = rank; m < nElim; m += gridDim.x) phaseC(a, l, 2 * m + 1, smem);
     if (l > 0 && !grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
 }

@@ -12,17 +12,18 @@ namespace bdss {
 enum { kSubA1 = 0, kSubA2 = 1, kSubB = 2, kSubC = 3 };
 
 template <typename T>
-__device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem, int *s_flag, TcState *tc) {
+__device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem, int *s_flag, TcState *tc,
+                          int rank) {
   const int n = a.p.n, d = a.d;
   const long long Nl = a.p.Nl[l];
   const long long nE = Nl / 2, nS = (Nl + 1) / 2;
   if (sub == kSubA1) {
-    for (long long m = blockIdx.x; m < nE; m += gridDim.x)
+    for (long long m = rank; m < nE; m += gridDim.x)
       if (!largeA1(a, l, 2 * m + 1, smem, s_flag)) return false;
   } else if (sub == kSubA2) {
     const int VT = vec_tile(sizeof(T));
     const int nvt = ((factor ? 2 * n : 0) + d + VT - 1) / VT;
-    for (long long t = blockIdx.x; t < nE * nvt; t += gridDim.x) {
+    for (long long t = rank; t < nE * nvt; t += gridDim.x) {
       const long long j = 2 * (t / nvt) + 1;
       const int v = (int)(t % nvt);
       if (v * VT < largeA2_vectors(a, l, j, factor)) largeA2(a, l, j, v, factor, smem);
@@ -32,7 +33,7 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
       if (tc && factor) {
         // D and E tiles on the tensor cores, RHS tiles on CUDA cores
         const int nTC = largeB_tc_tiles(n), nR = largeB_tiles(n, false, d), nTB = nTC + nR;
-        for (long long t = blockIdx.x; t < nS * nTB; t += gridDim.x) {
+        for (long long t = rank; t < nS * nTB; t += gridDim.x) {
           const long long k = t / nTB;
           const int u = (int)(t % nTB);
           if (u < nTC) {
@@ -45,9 +46,9 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
       }
     }
     const int nTB = largeB_tiles(n, factor, d);
-    for (long long t = blockIdx.x; t < nS * nTB; t += gridDim.x) largeB(a, l, t / nTB, (int)(t % nTB), factor, smem);
+    for (long long t = rank; t < nS * nTB; t += gridDim.x) largeB(a, l, t / nTB, (int)(t % nTB), factor, smem);
   } else {
-    for (long long m = blockIdx.x; m < nE; m += gridDim.x) largeC(a, l, 2 * m + 1, smem);
+    for (long long m = rank; m < nE; m += gridDim.x) largeC(a, l, 2 * m + 1, smem);
   }
   return true;
 }
@@ -57,21 +58,23 @@ __device__ void large_body(const Args<T> &a, int factor, int rhs, unsigned char 
                            TcState *tc) {
   T *smem = reinterpret_cast<T *>(smem_raw);
   int bar = 0;
+  const int rank = spread_rank(a.st, a.timeout_ns);
+  if (rank < 0) return;
   for (int l = 0; l < a.p.L; ++l) {
     if (factor) {
-      large_sub(a, l, kSubA1, true, smem, s_flag, tc);
+      large_sub(a, l, kSubA1, true, smem, s_flag, tc, rank);
       if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
     }
-    large_sub(a, l, kSubA2, factor != 0, smem, s_flag, tc);
+    large_sub(a, l, kSubA2, factor != 0, smem, s_flag, tc, rank);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
-    large_sub(a, l, kSubB, factor != 0, smem, s_flag, tc);
+    large_sub(a, l, kSubB, factor != 0, smem, s_flag, tc, rank);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
-  if (blockIdx.x == 0) largeTop(a, factor != 0, reinterpret_cast<double *>(smem_raw), s_flag);
+  if (rank == 0) largeTop(a, factor != 0, reinterpret_cast<double *>(smem_raw), s_flag);
   if (!rhs || a.p.L == 0) return;
   if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   for (int l = a.p.L - 1; l >= 0; --l) {
-    large_sub(a, l, kSubC, false, smem, s_flag, tc);
+    large_sub(a, l, kSubC, false, smem, s_flag, tc, rank);
     if (l > 0 && !grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
 }
@@ -103,7 +106,8 @@ __global__ void __launch_bounds__(kThreads) k_large_sub(const __grid_constant__ 
   TcState tc;
   const bool use_tc = std::is_same<T, float>::value && a.tf32 && factor && sub == kSubB;
   if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
-  large_sub(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, use_tc ? &tc : nullptr);
+  large_sub(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, use_tc ? &tc : nullptr,
+            (int)blockIdx.x);
   if (use_tc) tc_end(tc);
 }
 
