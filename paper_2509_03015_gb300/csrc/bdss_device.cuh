@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace bdss {
 
 constexpr int kMaxLevels = 48;
@@ -446,9 +448,12 @@ __host__ __device__ inline size_t smem_phaseA(int n, int d) {
   const int ld = ldstride(n);
   return (size_t)(2 * n + d) * ld + 8;
 }
-__host__ __device__ inline size_t smem_phaseB(int n, int d) {
+__host__ __device__ inline size_t smem_phaseB(int n, int d, int esz) {
   const int ld = ldstride(n);
-  return (size_t)(2 * n + 2 * d) * ld + 8;
+  const size_t generic = (size_t)(2 * n + 2 * d) * ld + 8;
+  if (esz != 4) return generic;
+  const size_t fp32_tiled = (size_t)2 * 64 * 68 + (size_t)2 * d * n + 8;  // phaseB_f32
+  return generic > fp32_tiled ? generic : fp32_tiled;
 }
 __host__ __device__ inline size_t smem_down(int n, int d) {
   const int ld = ldstride(n);
@@ -556,8 +561,112 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
 //   S_{s+2,s} = -W_R(s+1)^T W_L(s+1)  -> region l+1, slot k
 // W_R(s+1)^T is staged over W_R(s-1)^T once the first two are done.
 // ---------------------------------------------------------------------------
+// FP32 phase B (n <= 64, 256 threads): the W^T blocks are staged k-major
+// (sK[k][r] = W^T[r][k], rows of 68 floats, zero beyond n) so that each thread
+// computes a 4 x 4 tile of the 64 x 64 products with two 128-bit shared loads
+// per 16 FMAs; D is formed in full (only its lower triangle is stored).
+constexpr int kPB = 68;  // k-major row stride (floats), 16-byte aligned
+
+// g == nullptr stages zeros (a separator without that neighbour).
+__device__ __forceinline__ void stage_kmajor(float *sK, const float *g, int n) {
+  for (int e = threadIdx.x; e < kMaxN * kMaxN; e += blockDim.x) {
+    const int r = e >> 6, kk = e & 63;   // coalesced over k
+    sK[kk * kPB + r] = (g && r < n && kk < n) ? ldcg(g + (size_t)r * n + kk) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ void tile_acc_kmajor(float (&acc)[4][4], const float *sA, const float *sB, int n, int tr,
+                                                int tc) {
+  for (int kk = 0; kk < n; ++kk) {
+    const float4 x = *reinterpret_cast<const float4 *>(sA + kk * kPB + 4 * tr);
+    const float4 y = *reinterpret_cast<const float4 *>(sB + kk * kPB + 4 * tc);
+    const float xa[4] = {x.x, x.y, x.z, x.w}, yb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], yb[j], acc[i][j]);
+  }
+}
+
+__device__ inline void phaseB_f32(const Args<float> &a, int l, long long k, bool factor, float *smem) {
+  const int n = a.p.n, d = a.d;
+  const long long Nl = a.p.Nl[l];
+  const long long s = 2 * k;
+  const bool hasM = (s >= 2), hasP = (s + 1 < Nl), hasE = (s + 2 < Nl);
+  const long long orig = s << l;
+  const size_t nn = (size_t)n * n;
+  float *sK0 = smem;                        // W_R(s-1)^T, later W_R(s+1)^T, k-major
+  float *sK1 = sK0 + kMaxN * kPB;           // W_L(s+1)^T, k-major
+  float *sY = sK1 + kMaxN * kPB;            // y_{s-1}, y_{s+1}: [2][d][n]
+  const float *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  stage_kmajor(sK0, hasM ? W + (size_t)(s - 1) * nn : nullptr, n);
+  stage_kmajor(sK1, hasP ? W + (size_t)s * nn : nullptr, n);
+  if (d > 0)
+    for (int e = threadIdx.x; e < 2 * n * d; e += blockDim.x) {
+      const int side = e / (n * d), rem = e - side * n * d, q = rem / d, c = rem - q * d;
+      const bool have = side == 0 ? hasM : hasP;
+      const long long blk = side == 0 ? s - 1 : s + 1;
+      sY[(side * d + c) * n + q] = have ? ldcg(a.Y + (size_t)(blk << l) * n * d + rem) : 0.0f;
+    }
+  __syncthreads();
+  if (factor) {
+    float acc[4][4] = {};
+    if (hasM) tile_acc_kmajor(acc, sK0, sK0, n, tr, tc);
+    if (hasP) tile_acc_kmajor(acc, sK1, sK1, n, tr, tc);
+    float *Dg = a.Ld + (size_t)orig * nn;
+    const double *Ag = a.A_diag + (size_t)orig * nn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * tr + i, c = 4 * tc + j;
+        if (r < n && c <= r) {
+          const float base = (l == 0) ? 0.5f * ((float)ldcg(Ag + r * n + c) + (float)ldcg(Ag + c * n + r))
+                                      : ldcg(Dg + r * n + c);
+          Dg[r * n + c] = base - acc[i][j];
+        }
+      }
+  }
+  if (d > 0) {
+    const size_t boff = (size_t)orig * n * d;
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int r = e / d, c = e - r * d;
+      float acc;
+      if (l == 0 && a.B64) acc = (float)ldcg(a.B64 + boff + e);
+      else if (l == 0 && a.Bt) acc = ldcg(a.Bt + boff + e);
+      else acc = ldcg(a.Y + boff + e);
+      const float *ym = sY + (size_t)c * n, *yp = sY + (size_t)(d + c) * n;
+      for (int q = 0; q < n; ++q) acc = fmaf(-sK0[q * kPB + r], ym[q], fmaf(-sK1[q * kPB + r], yp[q], acc));
+      a.Y[boff + e] = acc;
+    }
+  }
+  if (factor && hasE) {
+    __syncthreads();
+    stage_kmajor(sK0, W + (size_t)(s + 1) * nn, n);
+    __syncthreads();
+    float acc[4][4] = {};
+    tile_acc_kmajor(acc, sK0, sK1, n, tr, tc);
+    float *En = a.Wb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * tr + i, c = 4 * tc + j;
+        if (r < n && c < n) En[r * n + c] = -acc[i][j];
+      }
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *smem) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (blockDim.x == kThreads) {
+      phaseB_f32(a, l, k, factor, smem);
+      return;
+    }
+  }
   const int n = a.p.n, ld = ldstride(n), d = a.d;
   const long long Nl = a.p.Nl[l];
   const long long s = 2 * k;
@@ -704,15 +813,23 @@ __device__ void phaseC(const Args<T> &a, int l, long long j, T *smem) {
   const T *WL = W + (size_t)(j - 1) * nn;   // W_L^T: WL[c][q] = W_L[q][c]
   const T *WR = W + (size_t)j * nn;
   const T *Yj = a.Y + (size_t)orig * nd;
-  // t[q][c] = y[q][c] - sum_p W_L[q][p] x_{j-1}[p][c] - sum_p W_R[q][p] x_{j+1}[p][c]
+  // t[q][c] = y[q][c] - sum_p W_L[q][p] x_{j-1}[p][c] - sum_p W_R[q][p] x_{j+1}[p][c];
+  // the W reads are issued 8 at a time ahead of their FMAs (L2 latency)
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
     const int c = e / n, q = e - c * n;
     T acc = ldcg(Yj + (size_t)q * d + c);
-    const T *xm = sXm + (size_t)c * ld;
-    for (int p = 0; p < n; ++p) acc = fma(-ldcg(WL + (size_t)p * n + q), xm[p], acc);
-    if (hasR) {
-      const T *xp = sXp + (size_t)c * ld;
-      for (int p = 0; p < n; ++p) acc = fma(-ldcg(WR + (size_t)p * n + q), xp[p], acc);
+    for (int side = 0; side < (hasR ? 2 : 1); ++side) {
+      const T *Wq = (side == 0 ? WL : WR) + q;
+      const T *x = (side == 0 ? sXm : sXp) + (size_t)c * ld;
+      int p = 0;
+      for (; p + 8 <= n; p += 8) {
+        T w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w[u] = ldcg(Wq + (size_t)(p + u) * n);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(-w[u], x[p + u], acc);
+      }
+      for (; p < n; ++p) acc = fma(-ldcg(Wq + (size_t)p * n), x[p], acc);
     }
     sT[c * ld + q] = acc;
   }

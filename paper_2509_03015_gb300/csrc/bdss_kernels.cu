@@ -12,8 +12,13 @@ namespace bdss {
 
 enum { kModeFactor = 1, kModeRhs = 2 };
 
+// Resident CTAs per SM the persistent kernel is compiled for (register
+// budget): FP64 is shared-memory limited to 3 at n = 64; FP32 fits 4.
+template <typename T> struct PersistentOcc { static constexpr int value = sizeof(T) == 4 ? 4 : 3; };
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_persistent(const __grid_constant__ Args<T> a, int mode) {
+__global__ void __launch_bounds__(kThreads, PersistentOcc<T>::value)
+    k_persistent(const __grid_constant__ Args<T> a, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_flag;
   T *smem = reinterpret_cast<T *>(smem_raw);
@@ -146,35 +151,39 @@ __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d
   }
 }
 
-// ||A||_inf of the full operator: one CTA per block row; each row's absolute
-// sum is split over kNormSplit threads and combined in shared memory.
+// ||A||_inf of the full operator, in FP32 arithmetic (it only scales the
+// refinement's stopping test, where a relative error of 1e-6 is immaterial,
+// and FP32 adds are ~60x cheaper than FP64 ones here): one CTA per block row,
+// each row's absolute sum split over kNormSplit threads and combined in
+// shared memory; the row maxima are stored as FP64 bit patterns.
 constexpr int kNormSplit = 4;
 
 __global__ void __launch_bounds__(kThreads) k_norm_A(long long N, int n, const double *A_diag,
                                                      const double *A_sub, DevStatus *st) {
-  __shared__ double rs[kThreads];
+  __shared__ float rs[kThreads];
   const size_t nn = (size_t)n * n;
   for (long long i = blockIdx.x; i < N; i += gridDim.x) {
-    for (int r = threadIdx.x; r < n; r += blockDim.x) rs[r] = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) rs[r] = 0.0f;
     __syncthreads();
     for (int t = threadIdx.x; t < n * kNormSplit; t += blockDim.x) {
       const int r = t / kNormSplit, q = t - r * kNormSplit;
-      double s = 0.0, sd = 0.0;
+      float s = 0.0f, sd = 0.0f;
       const double *D = A_diag + i * nn;
-      for (int p = q; p < n; p += kNormSplit) sd += fabs(__ldg(D + (size_t)r * n + p) + __ldg(D + (size_t)p * n + r));
+      for (int p = q; p < n; p += kNormSplit)
+        sd += fabsf((float)__ldg(D + (size_t)r * n + p) + (float)__ldg(D + (size_t)p * n + r));
       if (i > 0) {
         const double *S = A_sub + (i - 1) * nn;
-        for (int p = q; p < n; p += kNormSplit) s += fabs(__ldg(S + (size_t)r * n + p));
+        for (int p = q; p < n; p += kNormSplit) s += fabsf((float)__ldg(S + (size_t)r * n + p));
       }
       if (i + 1 < N) {
         const double *S = A_sub + i * nn;
-        for (int p = q; p < n; p += kNormSplit) s += fabs(__ldg(S + (size_t)p * n + r));
+        for (int p = q; p < n; p += kNormSplit) s += fabsf((float)__ldg(S + (size_t)p * n + r));
       }
-      atomicAdd(&rs[r], fma(0.5, sd, s));
+      atomicAdd(&rs[r], fmaf(0.5f, sd, s));
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x)
-      atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong(rs[r]));
+      atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong((double)rs[r]));
     __syncthreads();
   }
 }
@@ -261,7 +270,8 @@ cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, c
 template <typename T>
 size_t smem_bytes(int n, int d) {
   size_t w = smem_phaseA(n, d);
-  if (smem_phaseB(n, d) > w) w = smem_phaseB(n, d);
+  const size_t wb = smem_phaseB(n, d, (int)sizeof(T));
+  if (wb > w) w = wb;
   if (smem_down(n, d) > w) w = smem_down(n, d);
   size_t b = w * sizeof(T);
   if (smem_top_bytes(n, d) > b) b = smem_top_bytes(n, d);
