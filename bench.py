@@ -249,6 +249,22 @@ def run_reference(args, world, rank):
     }))
 
 
+def phase_split(stamps, L, launch_ms):
+    """Per-step times (us) of the last persistent launch from its grid-barrier
+    release stamps: phase A and phase B of each level, the top block, and the
+    downward levels L-1..1; "edges" is the launch time outside the stamped
+    span (start-up before the first barrier and the last downward level)."""
+    if len(stamps) < 1 + 2 * L:
+        return None
+    us = lambda i: (stamps[i] - stamps[i - 1]) / 1e3
+    out = {"A": [us(1 + 2 * l) for l in range(L)], "B": [us(2 + 2 * l) for l in range(L)]}
+    if len(stamps) >= 2 * L + 2:
+        out["top"] = us(2 * L + 1)
+        out["C"] = [us(2 * L + 1 + k) for k in range(1, len(stamps) - 2 * L - 1)]
+    out["edges"] = launch_ms * 1e3 - (stamps[-1] - stamps[0]) / 1e3
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,6 +339,7 @@ def main():
     value = world * args.steps / (elapsed_ms * 1e-3)
     clocks = clk.summary()
 
+    phases = phase_split(solver.trace(), solver.plan_levels, launch_ms)
     tally = accounting.thomas_flops(N, n, d)
     crf = accounting.cr_flops(N, n, d)
     alg = tally["factor"] + tally["solve"]
@@ -349,6 +366,7 @@ def main():
                                         "a DFMA loop measured 1.194 TFLOP/s on this GPU"},
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
+        "phase_us": phases,
     }
 
     if not args.no_extras:

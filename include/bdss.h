@@ -154,6 +154,16 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
 
+/* Phase trace of the last launch that ran grid barriers (a persistent factor
+ * or solve pass): release_ns[i] = %globaltimer (ns) when grid barrier i was
+ * released; barrier 0 is the start-up barrier, then for each level l the
+ * barriers after its elimination (phase A) and separator (phase B) steps, then
+ * one per downward level.  Differences of consecutive stamps are the time of
+ * each step.  Writes min(*count, capacity) entries to the host array
+ * release_ns and the number recorded (at most 256) to *count (may be NULL).
+ * The paper reports wall-clock phases only; this is the per-level split. */
+bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity, int32_t *count);
+
 /* Self-check of the tensor-core Schur tile used by BDSS_TF32_IR for n > 64:
  * one 128 x 128 tile C = A B^T with K = 256 computed with TMA-fed
  * tcgen05.mma (3xTF32 split) and compared on the device with an FP64 product

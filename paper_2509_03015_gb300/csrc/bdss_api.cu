@@ -52,6 +52,8 @@ struct bdss_ctx {
   // stats of the last call
   int64_t launches = 0;
   int64_t barriers = 0;
+  int trace_count = 0;               // barrier stamps of the last persistent launch
+  long long trace[kTraceSlots] = {};
 };
 
 static constexpr int kLogdetGrid = 256;
@@ -95,6 +97,12 @@ static bdss_status finish(bdss_ctx *h, bdss_info *info) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e);
   const int st = h->hst->status;
+  if (h->hst->trace[0] != 0) {  // a launch with grid barriers: keep its stamps
+    int c = 0;
+    while (c < kTraceSlots && h->hst->trace[c] != 0) ++c;
+    memcpy(h->trace, h->hst->trace, sizeof(h->trace));
+    h->trace_count = c;
+  }
   if (info && st == BDSS_ERR_NOT_SPD) {
     info->level = h->hst->level;
     info->block = h->hst->block;
@@ -118,6 +126,7 @@ static Args<T> base_args(bdss_ctx *h) {
   a.st = h->dst;
   a.timeout_ns = h->timeout_ns;
   a.skip_barrier = h->skip_barrier;
+  a.capacity = h->bps * h->sms;
   a.tf32 = h->tf32;
   a.tmap_w = h->d_tmap;
   return a;
@@ -164,8 +173,14 @@ template <typename T>
 static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool rhs) {
   const Plan &p = h->plan;
   if (h->large) return run_levels_large<T>(h, a, factor, rhs);
+  const int cap = h->bps * h->sms;
   if (h->persistent) {
-    const int grid = grid_for(h, (p.N + 1) / 2);
+    long long most = 1;  // tasks of the busiest step
+    for (int l = 0; l < p.L; ++l) {
+      most = std::max(most, (p.Nl[l] / 2) * parts_A<T>(p, l, factor, cap));
+      most = std::max(most, ((p.Nl[l] + 1) / 2) * parts_B<T>(p, l, factor, cap));
+    }
+    const int grid = grid_for(h, most);
     h->launches += 1;
     int bars = 1 + 2 * p.L;  // the spread-rank barrier, then two per level
     if (rhs && p.L > 0) bars += 1 + (p.L - 1);
@@ -177,8 +192,11 @@ static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool r
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < p.L && e == cudaSuccess; ++l) {
     const long long nElim = p.Nl[l] / 2, nSep = (p.Nl[l] + 1) / 2;
-    e = launch_phaseA<T>(b, l, factor ? 1 : 0, grid_for(h, nElim), h->smem, h->stream);
-    if (e == cudaSuccess) e = launch_phaseB<T>(b, l, factor ? 1 : 0, grid_for(h, nSep), h->smem, h->stream);
+    e = launch_phaseA<T>(b, l, factor ? 1 : 0, grid_for(h, nElim * parts_A<T>(p, l, factor, cap)), h->smem,
+                         h->stream);
+    if (e == cudaSuccess)
+      e = launch_phaseB<T>(b, l, factor ? 1 : 0, grid_for(h, nSep * parts_B<T>(p, l, factor, cap)), h->smem,
+                           h->stream);
     h->launches += 2;
   }
   if (e == cudaSuccess) e = launch_top<T>(b, factor ? 1 : 0, h->smem, h->stream);
@@ -532,6 +550,14 @@ bdss_status bdss_tc_selftest(double *max_rel_err) {
   cudaError_t e = run_tc_selftest(max_rel_err, &st);
   if (e != cudaSuccess) return cuda_fail(e);
   return (bdss_status)st;
+}
+
+bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity, int32_t *count) {
+  if (!h || capacity < 0 || (capacity > 0 && !release_ns)) return BDSS_ERR_INVALID_ARG;
+  const int c = std::min(h->trace_count, (int)capacity);
+  for (int i = 0; i < c; ++i) release_ns[i] = h->trace[i];
+  if (count) *count = h->trace_count;
+  return BDSS_OK;
 }
 
 const char *bdss_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda_error); }

@@ -267,7 +267,8 @@ static cudaError_t batch_enqueue(bdss_batch_ctx *b) {
   a.timeout_ns = b->timeout_ns;
   cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, (size_t)b->total_stages * sizeof(unsigned), b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, (size_t)b->K * sizeof(DevStatus), b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemset2DAsync(b->d_status, sizeof(DevStatus), 0, kStatusCoreBytes, (size_t)b->K, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_t, 0xff, (size_t)b->K * sizeof(unsigned long long), b->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(b->d_t + b->K, 0, (size_t)b->K * sizeof(unsigned long long), b->stream);
@@ -424,8 +425,8 @@ bdss_status bdss_batch_launch(bdss_batch b, int32_t use_graph) {
 
 bdss_status bdss_batch_wait(bdss_batch b, bdss_info *info_k, double *latency_us_k) {
   if (!b) return BDSS_ERR_INVALID_ARG;
-  cudaError_t e = cudaMemcpyAsync(b->h_status, b->d_status, (size_t)b->K * sizeof(DevStatus),
-                                  cudaMemcpyDeviceToHost, b->stream);
+  cudaError_t e = cudaMemcpy2DAsync(b->h_status, sizeof(DevStatus), b->d_status, sizeof(DevStatus), kStatusCoreBytes,
+                                    (size_t)b->K, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->h_t, b->d_t, (size_t)2 * b->K * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         b->stream);

@@ -22,6 +22,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <type_traits>
@@ -36,6 +37,7 @@ enum { kStOk = 0, kStNotSPD = 2, kStTimeout = 6 };
 
 constexpr int kSmSlots = 256;  // SM-id table of the spread rank
 constexpr int kCtaSlots = 8;   // co-resident CTA classes per SM
+constexpr int kTraceSlots = 256;  // grid-barrier release stamps kept per launch
 
 struct DevStatus {
   unsigned int bar_count;  // arrivals at the current grid barrier
@@ -47,7 +49,11 @@ struct DevStatus {
   unsigned long long nrm[4];  // residual kernel: bit patterns of max-norms (>= 0)
   unsigned int sm_count[kSmSlots];    // CTAs seen per SM (spread rank)
   unsigned int slot_count[kCtaSlots]; // CTAs per arrival slot (spread rank)
+  long long trace[kTraceSlots];       // %globaltimer (ns) at each barrier release
 };
+// Leading bytes of DevStatus that kernels without grid barriers use (status,
+// pivot position, norms): the batched path copies only these per instance.
+constexpr size_t kStatusCoreBytes = offsetof(DevStatus, sm_count);
 
 struct Plan {
   long long N;
@@ -76,6 +82,7 @@ struct Args {
   DevStatus *st;
   long long timeout_ns;
   int skip_barrier;      // test hook: 1-based barrier index CTA 0 skips
+  int capacity;          // CTAs of a full persistent grid (tail-level splits)
   int tf32;              // large FP32 path: Schur products on tcgen05 (3xTF32)
   const CUtensorMap *tmap_w;  // TMA map of Wb as (slots * n) rows x n FP32 columns
 };
@@ -127,6 +134,7 @@ static __device__ __noinline__ bool grid_barrier(DevStatus *st, long long timeou
         __threadfence();
         const unsigned prev = atomicAdd(&st->bar_count, 1u);
         if (prev == gridDim.x - 1) {
+          if (index >= 0 && index < kTraceSlots) st->trace[index] = global_ns();
           atomicExch(&st->bar_count, 0u);
           __threadfence();
           atomicAdd(&st->bar_gen, 1u);
@@ -464,32 +472,88 @@ __host__ __device__ inline size_t smem_top_bytes(int n, int d) {
   return ((size_t)n * ld + (size_t)d * ld + 8) * sizeof(double);
 }
 
+// CTAs per block at a level with few blocks: the persistent grid holds
+// `capacity` CTAs; when a level has fewer blocks than that, each block's
+// work is split over up to max_parts CTAs (one CTA per block would leave most
+// SMs idle while the level's latency sets the pace).
+__host__ __device__ inline int split_parts(long long items, int capacity, int max_parts) {
+  if (items <= 0) return 1;
+  const long long k = (long long)capacity / items;
+  if (k < 2) return 1;
+  return k > max_parts ? max_parts : (int)k;
+}
+constexpr int kMaxPartsA = 4;  // coupling columns of phase A over CTAs
+constexpr int kMaxPartsB = 8;  // output entries of the FP64 phase B over CTAs
+
+template <typename T> __host__ __device__ inline int parts_A(const Plan &p, int l, bool factor, int capacity) {
+  return factor ? split_parts(p.Nl[l] / 2, capacity, kMaxPartsA) : 1;
+}
+template <typename T> __host__ __device__ inline int parts_B(const Plan &p, int l, bool factor, int capacity) {
+  return (factor && sizeof(T) == 8) ? split_parts((p.Nl[l] + 1) / 2, capacity, kMaxPartsB) : 1;
+}
+
+// s[(c - c0)*ld + i] = g[i][c] for c0 <= c < c1 (columns of an n x n block).
+template <typename T, typename S>
+__device__ void stage_col_range(T *s, int ld, const S *g, int n, int c0, int c1) {
+  const int w = c1 - c0;
+  for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
+    const int i = e / w, c = e - i * w;
+    s[c * ld + i] = (T)ldcg(g + (size_t)i * n + c0 + c);
+  }
+}
+// s[(r - r0)*ld + c] = g[r][c] for r0 <= r < r1 (rows of an n x n block).
+template <typename T, typename S>
+__device__ void stage_row_range(T *s, int ld, const S *g, int n, int r0, int r1) {
+  for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    s[r * ld + c] = (T)ldcg(g + (size_t)(r0 + r) * n + c);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Phase A: eliminated position j (odd) of level l.
 //   factor:  L_j = chol(D_j); W_L^T, W_R^T via forward substitution (trsm);
 //   rhs:     y_j = L_j^{-1} b_j (Algorithm 5's interior solve, fused).
 // With factor == false only the RHS part runs, using the stored L_j.
+// The 2n coupling columns (n of W_L, then n of W_R) may be split over
+// `nparts` CTAs: each factors D_j itself (the same arithmetic, so the same
+// L_j), solves its contiguous share of the columns, and part 0 alone stores
+// L_j and handles the right-hand sides.  Every column is solved by the same
+// operations whatever the split.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *smem, int *s_flag) {
-  const int n = a.p.n, ld = ldstride(n), d = a.d;
+__device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *smem, int *s_flag, int part = 0,
+                       int nparts = 1) {
+  const int n = a.p.n, ld = ldstride(n);
+  const int d = part == 0 ? a.d : 0;
   const long long Nl = a.p.Nl[l];
   const bool hasR = (j + 1 < Nl);
   const long long orig = j << l;
   const size_t nn = (size_t)n * n;
+  const int nW = factor ? (hasR ? 2 * n : n) : 0;
+  const int c0 = (int)((long long)part * nW / nparts), c1 = (int)((long long)(part + 1) * nW / nparts);
+  const int l0 = c0, l1 = min(c1, n);                   // W_L columns of this part
+  const int r0 = max(c0, n) - n, r1 = c1 - n;           // W_R columns (rows of A_{j+1,j})
+  if (part > 0 && c1 <= c0) return true;                // nothing to solve here
   T *sL = smem;
-  T *sV = sL + (size_t)n * ld;                         // n coupling vectors (one pass)
+  T *sV = sL + (size_t)n * ld;                          // up to n coupling vectors (one pass)
   T *sB = sV + (size_t)(factor ? n : 0) * ld;           // d RHS vectors
-  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   const T *E = (l == 0) ? nullptr : a.Wb + (size_t)a.p.off[l] * nn;
   T *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const T *EL = (l == 0) ? nullptr : E + (size_t)(j - 1) * nn;
+  const T *ER = (l == 0) ? nullptr : E + (size_t)j * nn;
+  const double *AL = a.A_sub ? a.A_sub + (size_t)(j - 1) * nn : nullptr;
+  const double *AR = a.A_sub ? a.A_sub + (size_t)j * nn : nullptr;
 
   if (factor) {
     if (l == 0) stage_sym_lower(sL, ld, a.A_diag + orig * nn, n);
     else stage_lower(sL, ld, a.Ld + orig * nn, n);
-    // pass 1 vectors: the columns of E_l[j-1] = A_{j,j-1}
-    if (l == 0) stage_cols(sV, ld, a.A_sub + (size_t)(j - 1) * nn, n, n);
-    else stage_cols(sV, ld, E + (size_t)(j - 1) * nn, n, n);
+    // pass 1 vectors: columns of E_l[j-1] = A_{j,j-1}
+    if (l1 > l0) {
+      if (l == 0) stage_col_range(sV, ld, AL, n, l0, l1);
+      else stage_col_range(sV, ld, EL, n, l0, l1);
+    }
   } else {
     stage_lower(sL, ld, a.Ld + orig * nn, n);
   }
@@ -507,25 +571,26 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       __syncthreads();
       return false;
     }
-    T *Lg = a.Ld + orig * nn;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int r = e / n, c = e - r * n;
-      if (c <= r) Lg[e] = sL[r * ld + c];
+    if (part == 0) {
+      T *Lg = a.Ld + orig * nn;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        if (c <= r) Lg[e] = sL[r * ld + c];
+      }
     }
   }
   // pass 1: W_L over all warps, then the RHS vectors by one warp
   // (warp-cooperative)
-  if (factor) trsv_fwd_rows(sL, ld, n, sV, n);
+  if (l1 > l0) trsv_fwd_rows(sL, ld, n, sV, l1 - l0);
   if (d > 0) {
     if (warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
     __syncthreads();
   }
-  (void)nwarps;
-  if (factor) {
+  if (l1 > l0) {
     T *WL = W + (size_t)(j - 1) * nn;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (l1 - l0) * n; e += blockDim.x) {
       const int c = e / n, i = e - c * n;
-      WL[e] = sV[c * ld + i];
+      WL[(size_t)(l0 + c) * n + i] = sV[c * ld + i];
     }
   }
   if (d > 0) {
@@ -535,18 +600,18 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       Yj[e] = sB[c * ld + i];
     }
   }
-  if (factor && hasR) {
+  if (r1 > r0) {
     // pass 2: W_R from the rows of E_l[j] = A_{j+1,j}
     __syncthreads();
-    if (l == 0) stage_rows(sV, ld, a.A_sub + (size_t)j * nn, n);
-    else stage_rows(sV, ld, E + (size_t)j * nn, n);
+    if (l == 0) stage_row_range(sV, ld, AR, n, r0, r1);
+    else stage_row_range(sV, ld, ER, n, r0, r1);
     __syncthreads();
-    trsv_fwd_rows(sL, ld, n, sV, n);
+    trsv_fwd_rows(sL, ld, n, sV, r1 - r0);
     __syncthreads();
     T *WR = W + (size_t)j * nn;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
       const int c = e / n, i = e - c * n;
-      WR[e] = sV[c * ld + i];
+      WR[(size_t)(r0 + c) * n + i] = sV[c * ld + i];
     }
   }
   __syncthreads();
@@ -659,10 +724,14 @@ __device__ inline void phaseB_f32(const Args<float> &a, int l, long long k, bool
   __syncthreads();
 }
 
+// FP64 / generic phase B.  Its outputs -- the lower triangle of S_ss, the
+// n x d RHS update and the n x n coupling S_{s+2,s} -- may be split over
+// `nparts` CTAs, each taking a contiguous share of each; every entry is
+// formed by the same operations whatever the split.
 template <typename T>
-__device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *smem) {
+__device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *smem, int part = 0, int nparts = 1) {
   if constexpr (std::is_same<T, float>::value) {
-    if (blockDim.x == kThreads) {
+    if (blockDim.x == kThreads && nparts == 1) {
       phaseB_f32(a, l, k, factor, smem);
       return;
     }
@@ -673,13 +742,17 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
   const bool hasM = (s >= 2), hasP = (s + 1 < Nl), hasE = (s + 2 < Nl);
   const long long orig = s << l;
   const size_t nn = (size_t)n * n;
+  const int ntri = n * (n + 1) / 2;
+  const int t0 = (int)((long long)part * ntri / nparts), t1 = (int)((long long)(part + 1) * ntri / nparts);
+  const int b0 = (int)((long long)part * n * d / nparts), b1 = (int)((long long)(part + 1) * n * d / nparts);
+  const int e0 = (int)((long long)part * n * n / nparts), e1 = (int)((long long)(part + 1) * n * n / nparts);
   T *sW0 = smem;                      // W_R(s-1)^T, later W_R(s+1)^T
   T *sW1 = sW0 + (size_t)n * ld;      // W_L(s+1)^T
   T *sY = sW1 + (size_t)n * ld;       // y_{s-1}, y_{s+1} as d vectors each
   const T *W = a.Wb + (size_t)a.p.off[l] * nn;
   if (hasM) stage_rows(sW0, ld, W + (size_t)(s - 1) * nn, n);
   if (hasP) stage_rows(sW1, ld, W + (size_t)s * nn, n);
-  if (d > 0) {
+  if (d > 0 && b1 > b0) {
     if (hasM) stage_cols(sY, ld, a.Y + (size_t)((s - 1) << l) * n * d, n, d);
     if (hasP) stage_cols(sY + (size_t)d * ld, ld, a.Y + (size_t)((s + 1) << l) * n * d, n, d);
   }
@@ -688,8 +761,7 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
     // diagonal update, lower triangle
     T *Dg = a.Ld + (size_t)orig * nn;
     const double *Ag = a.A_diag + (size_t)orig * nn;
-    const int ntri = n * (n + 1) / 2;
-    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
       int r, c;
       tri_index(t, r, c);
       T acc;
@@ -708,7 +780,7 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
   }
   if (d > 0) {
     const size_t boff = (size_t)orig * n * d;
-    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+    for (int e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
       const int r = e / d, c = e - r * d;
       T acc;
       if (l == 0 && a.B64) acc = (T)ldcg(a.B64 + boff + e);
@@ -725,12 +797,12 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
       a.Y[boff + e] = acc;
     }
   }
-  if (factor && hasE) {
+  if (factor && hasE && e1 > e0) {
     __syncthreads();
     stage_rows(sW0, ld, W + (size_t)(s + 1) * nn, n);
     __syncthreads();
     T *En = a.Wb + ((size_t)a.p.off[l + 1] + (size_t)k) * nn;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const int r = e / n, c = e - r * n;
       const T *wr = sW0 + r * ld, *wc = sW1 + c * ld;
       T acc = T(0);

@@ -30,10 +30,14 @@ __global__ void __launch_bounds__(kThreads, PersistentOcc<T>::value)
   for (int l = 0; l < a.p.L; ++l) {
     const long long Nl = a.p.Nl[l];
     const long long nElim = Nl / 2, nSep = (Nl + 1) / 2;
-    for (long long m = rank; m < nElim; m += gridDim.x)
-      if (!phaseA(a, l, 2 * m + 1, factor, smem, &s_flag)) break;
+    // task t -> block t % count, part t / count: the parts of one block sit
+    // `count` ranks apart, i.e. on different SMs
+    const int pA = parts_A<T>(a.p, l, factor, a.capacity);
+    for (long long t = rank; t < nElim * pA; t += gridDim.x)
+      if (!phaseA(a, l, 2 * (t % nElim) + 1, factor, smem, &s_flag, (int)(t / nElim), pA)) break;
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
-    for (long long k = rank; k < nSep; k += gridDim.x) phaseB(a, l, k, factor, smem);
+    const int pB = parts_B<T>(a.p, l, factor, a.capacity);
+    for (long long t = rank; t < nSep * pB; t += gridDim.x) phaseB(a, l, t % nSep, factor, smem, (int)(t / nSep), pB);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
   if (rank == 0) top_block(a, factor, reinterpret_cast<double *>(smem_raw), &s_flag);
@@ -56,8 +60,11 @@ __global__ void __launch_bounds__(kThreads) k_phaseA(const __grid_constant__ Arg
   __shared__ int s_flag;
   if (status_set(a.st)) return;
   const long long nElim = a.p.Nl[l] / 2;
-  for (long long m = blockIdx.x; m < nElim; m += gridDim.x)
-    if (!phaseA(a, l, 2 * m + 1, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag)) return;
+  const int pA = parts_A<T>(a.p, l, factor != 0, a.capacity);
+  for (long long t = blockIdx.x; t < nElim * pA; t += gridDim.x)
+    if (!phaseA(a, l, 2 * (t % nElim) + 1, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, (int)(t / nElim),
+                pA))
+      return;
 }
 
 template <typename T>
@@ -65,8 +72,9 @@ __global__ void __launch_bounds__(kThreads) k_phaseB(const __grid_constant__ Arg
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (status_set(a.st)) return;
   const long long nSep = (a.p.Nl[l] + 1) / 2;
-  for (long long k = blockIdx.x; k < nSep; k += gridDim.x)
-    phaseB(a, l, k, factor != 0, reinterpret_cast<T *>(smem_raw));
+  const int pB = parts_B<T>(a.p, l, factor != 0, a.capacity);
+  for (long long t = blockIdx.x; t < nSep * pB; t += gridDim.x)
+    phaseB(a, l, t % nSep, factor != 0, reinterpret_cast<T *>(smem_raw), (int)(t / nSep), pB);
 }
 
 template <typename T>

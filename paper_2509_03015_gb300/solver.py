@@ -114,6 +114,23 @@ class Solver:
         _lib.check(self.lib.bdss_last_launch_stats(self.h, ctypes.byref(k), ctypes.byref(b)), "bdss_last_launch_stats")
         return k.value, b.value
 
+    @property
+    def plan_levels(self):
+        """Levels L with eliminations (N_{l+1} = ceil(N_l / 2) down to 1)."""
+        L, m = 0, self.N
+        while m > 1:
+            m, L = (m + 1) // 2, L + 1
+        return L
+
+    def trace(self):
+        """Grid-barrier release times (ns, device clock) of the last
+        persistent pass: start-up, then phase A / phase B of each level, then
+        one per downward level."""
+        buf = (ctypes.c_int64 * 256)()
+        cnt = ctypes.c_int32()
+        _lib.check(self.lib.bdss_last_trace(self.h, buf, 256, ctypes.byref(cnt)), "bdss_last_trace")
+        return [buf[i] for i in range(min(cnt.value, 256))]
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.bdss_destroy(self.h)
