@@ -291,6 +291,131 @@ __device__ int chol_staged(T *s, int ld, int n, int *s_flag) {
   return *s_flag;
 }
 
+// Packed lower-triangle index t -> (a, b), b <= a < kMaxN, as (a << 8) | b:
+// a 4 KB read-only table (L1-resident) instead of a square root per element.
+struct TriTable {
+  unsigned short v[kMaxN * (kMaxN + 1) / 2];
+};
+constexpr TriTable make_tri_table() {
+  TriTable t{};
+  int k = 0;
+  for (int a = 0; a < kMaxN; ++a)
+    for (int b = 0; b <= a; ++b) t.v[k++] = (unsigned short)((a << 8) | b);
+  return t;
+}
+static __device__ const TriTable g_tri = make_tri_table();
+
+// Barrier among the update warps only (warps 1.., named barrier 1).
+__device__ __forceinline__ void update_warps_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x - 32) : "memory");
+}
+
+// Cholesky of the staged lower triangle fused with forward substitution
+// (Algorithm 1's potrf and trsm in one right-looking sweep):
+//   L = chol(S) in place (diagonal <- 1 / L_kk), and for every staged vector
+//   w (rows of V1 and V2, stride ld): w <- L^{-1} w.
+// Warp 0 finishes the next column (its update and pivot) while the other
+// warps apply the current column to the trailing triangle and to the
+// vectors, so one pivot latency per column is exposed instead of a pivot
+// plus a barrier-separated update and a separate substitution.  Each entry
+// receives the same fused multiply-adds in the same order as the
+// column-by-column factorisation followed by row-by-row substitution.
+// Needs blockDim.x >= 64 (a multiple of 32).  Returns the first failing
+// column + 1, or 0.
+template <typename T>
+__device__ int chol_fused(T *s, int ld, int n, T *V1, int nv1, T *V2, int nv2, int *s_flag) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nv = nv1 + nv2;
+  int bad = 0;
+  if (tid < 32) {  // column 0
+    const T dkk = s[0];
+    const bool ok = (dkk > T(0)) && isfinite(dkk);
+    const T r = rsqrt_nr(ok ? dkk : T(1));
+    for (int i = 1 + lane; i < n; i += 32) s[i * ld] *= r;
+    if (lane == 0) {
+      s[0] = r;
+      *s_flag = ok ? 0 : 1;
+      bad = ok ? 0 : 1;
+    }
+  }
+  if (__syncthreads_or(bad)) return 1;
+  const int ut = tid - 32, un = blockDim.x - 32;  // update-thread index / count
+  for (int k = 0; k + 1 < n; ++k) {
+    if (tid < 32) {
+      // column k+1: apply column k, pivot, scale (rows k+1+lane, k+33+lane)
+      const int i0 = k + 1 + lane, i1 = i0 + 32;
+      const T lk = s[(k + 1) * ld + k];
+      T v0 = T(0), v1 = T(0);
+      if (i0 < n) v0 = fma(-s[i0 * ld + k], lk, s[i0 * ld + k + 1]);
+      if (i1 < n) v1 = fma(-s[i1 * ld + k], lk, s[i1 * ld + k + 1]);
+      const T dkk = __shfl_sync(0xffffffffu, v0, 0);
+      const bool ok = (dkk > T(0)) && isfinite(dkk);
+      const T r = rsqrt_nr(ok ? dkk : T(1));
+      if (i0 < n) s[i0 * ld + k + 1] = lane == 0 ? r : v0 * r;
+      if (i1 < n) s[i1 * ld + k + 1] = v1 * r;
+      if (lane == 0 && !ok) {
+        *s_flag = k + 2;
+        bad = 1;
+      }
+    } else {
+      // vectors: w[k] <- w[k] / L_kk, then w[j] -= w[k] L[j][k] for j > k;
+      // trailing triangle j >= k+2: S[i][j] -= L[i][k] L[j][k]
+      const T rk = s[k * ld + k];
+      for (int v = ut; v < nv; v += un) {
+        T *w = v < nv1 ? V1 + v * ld : V2 + (v - nv1) * ld;
+        w[k] *= rk;
+      }
+      update_warps_sync();
+      const int m2 = n - k - 2, cnt = m2 * (m2 + 1) / 2;
+      const int m1 = n - k - 1, tot = cnt + nv * m1;
+      // (v, j) of vector entry u: v = floor(u / m1) through an FP32
+      // reciprocal (exact here: u < 2^13 and the quotient is at least
+      // 1/(2 m1) away from the next integer)
+      const float inv_m1 = 1.0f / (float)m1;
+      // kU independent entries per pass, all loads before any store (the
+      // stores may not be reordered above later loads of the same array)
+      constexpr int kU = sizeof(T) == 8 ? 2 : 4;
+      for (int t = ut; t < tot; t += kU * un) {
+        T *dst[kU];
+        T x[kU], y[kU], z[kU];
+#pragma unroll
+        for (int q = 0; q < kU; ++q) {
+          const int tq = t + q * un;
+          if (tq < tot) {
+            if (tq < cnt) {
+              const unsigned ab = __ldg(&g_tri.v[tq]);
+              const int i = k + 2 + (int)(ab >> 8), j = k + 2 + (int)(ab & 255u);
+              dst[q] = s + i * ld + j;
+              x[q] = s[i * ld + k];
+              y[q] = s[j * ld + k];
+            } else {
+              const int u = tq - cnt;
+              const int v = (int)(((float)u + 0.5f) * inv_m1);
+              const int j = k + 1 + (u - v * m1);
+              T *w = v < nv1 ? V1 + v * ld : V2 + (v - nv1) * ld;
+              dst[q] = w + j;
+              x[q] = w[k];
+              y[q] = s[j * ld + k];
+            }
+            z[q] = *dst[q];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kU; ++q)
+          if (t + q * un < tot) *dst[q] = fma(-x[q], y[q], z[q]);
+      }
+    }
+    if (__syncthreads_or(bad)) return *s_flag;
+  }
+  const T rl = s[(n - 1) * ld + n - 1];
+  for (int v = tid; v < nv; v += blockDim.x) {
+    T *w = v < nv1 ? V1 + v * ld : V2 + (v - nv1) * ld;
+    w[n - 1] *= rl;
+  }
+  __syncthreads();
+  return 0;
+}
+
 // Warp-cooperative substitutions for a few right-hand sides (n <= 64): lane
 // l owns rows l and l + 32 of every vector (vectors are rows of V, stride
 // ld); each pivot is finished by its owning lane and broadcast by shuffle,
@@ -482,7 +607,7 @@ __host__ __device__ inline int split_parts(long long items, int capacity, int ma
   if (k < 2) return 1;
   return k > max_parts ? max_parts : (int)k;
 }
-constexpr int kMaxPartsA = 4;  // coupling columns of phase A over CTAs
+constexpr int kMaxPartsA = 8;  // coupling columns of phase A over CTAs
 constexpr int kMaxPartsB = 8;  // output entries of the FP64 phase B over CTAs
 
 template <typename T> __host__ __device__ inline int parts_A(const Plan &p, int l, bool factor, int capacity) {
@@ -546,13 +671,19 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
   const double *AL = a.A_sub ? a.A_sub + (size_t)(j - 1) * nn : nullptr;
   const double *AR = a.A_sub ? a.A_sub + (size_t)j * nn : nullptr;
 
+  // vectors solved along with the factorisation: this part's W_L columns,
+  // or its W_R columns if it has no W_L ones; W_R columns of a part that
+  // has both follow in a second pass
+  const bool passL = l1 > l0, fuseR = !passL && r1 > r0;
   if (factor) {
     if (l == 0) stage_sym_lower(sL, ld, a.A_diag + orig * nn, n);
     else stage_lower(sL, ld, a.Ld + orig * nn, n);
-    // pass 1 vectors: columns of E_l[j-1] = A_{j,j-1}
-    if (l1 > l0) {
+    if (passL) {  // columns of E_l[j-1] = A_{j,j-1}
       if (l == 0) stage_col_range(sV, ld, AL, n, l0, l1);
       else stage_col_range(sV, ld, EL, n, l0, l1);
+    } else if (fuseR) {  // rows of E_l[j] = A_{j+1,j}
+      if (l == 0) stage_row_range(sV, ld, AR, n, r0, r1);
+      else stage_row_range(sV, ld, ER, n, r0, r1);
     }
   } else {
     stage_lower(sL, ld, a.Ld + orig * nn, n);
@@ -564,8 +695,27 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
     else stage_cols(sB, ld, a.Y + boff, n, d);
   }
   __syncthreads();
+  const int nvf = passL ? l1 - l0 : (fuseR ? r1 - r0 : 0);
   if (factor) {
-    const int bad = chol_staged(sL, ld, n, s_flag);
+    int bad;
+    if (blockDim.x >= 64 && sizeof(T) == 8) {
+      bad = chol_fused(sL, ld, n, sV, nvf, sB, d, s_flag);
+    } else if (blockDim.x >= 64) {
+      // FP32: short FMA latency makes the separate substitution cheap
+      bad = chol_fused(sL, ld, n, sV, 0, sB, 0, s_flag);
+      if (!bad) {
+        if (nvf > 0) trsv_fwd_rows(sL, ld, n, sV, nvf);
+        if (d > 0 && warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
+        __syncthreads();
+      }
+    } else {
+      bad = chol_staged(sL, ld, n, s_flag);
+      if (!bad) {
+        if (nvf > 0) trsv_fwd_rows(sL, ld, n, sV, nvf);
+        if (d > 0) trsv_fwd_warp(sL, ld, n, sB, d);
+        __syncthreads();
+      }
+    }
     if (bad) {
       if (threadIdx.x == 0) set_status(a.st, kStNotSPD, l, orig);
       __syncthreads();
@@ -578,19 +728,16 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
         if (c <= r) Lg[e] = sL[r * ld + c];
       }
     }
-  }
-  // pass 1: W_L over all warps, then the RHS vectors by one warp
-  // (warp-cooperative)
-  if (l1 > l0) trsv_fwd_rows(sL, ld, n, sV, l1 - l0);
-  if (d > 0) {
+  } else if (d > 0) {
     if (warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
     __syncthreads();
   }
-  if (l1 > l0) {
-    T *WL = W + (size_t)(j - 1) * nn;
-    for (int e = threadIdx.x; e < (l1 - l0) * n; e += blockDim.x) {
+  if (nvf > 0) {
+    T *Wd = W + (size_t)(passL ? j - 1 : j) * nn;
+    const int c0w = passL ? l0 : r0;
+    for (int e = threadIdx.x; e < nvf * n; e += blockDim.x) {
       const int c = e / n, i = e - c * n;
-      WL[(size_t)(l0 + c) * n + i] = sV[c * ld + i];
+      Wd[(size_t)(c0w + c) * n + i] = sV[c * ld + i];
     }
   }
   if (d > 0) {
@@ -600,7 +747,7 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       Yj[e] = sB[c * ld + i];
     }
   }
-  if (r1 > r0) {
+  if (passL && r1 > r0) {
     // pass 2: W_R from the rows of E_l[j] = A_{j+1,j}
     __syncthreads();
     if (l == 0) stage_row_range(sV, ld, AR, n, r0, r1);
