@@ -43,6 +43,7 @@ struct bdss_ctx {
   const double *A_diag = nullptr;  // remembered for the FP64 residual (mixed)
   const double *A_sub = nullptr;
   double normA = 0.0;
+  bool norm_valid = false;
   // options
   long long timeout_ns = 10000000000LL;
   int persistent = 1;
@@ -391,18 +392,11 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
       a.x_accumulate = 0;
     }
     e = run_levels<float>(h, a, true, rhs);
-    if (e == cudaSuccess) {
-      e = launch_norm_A(h->N, h->n, A_diag, A_sub, h->dst, grid_for(h, h->N), h->stream);
-      h->launches += 1;
-    }
   }
   if (e != cudaSuccess) return cuda_fail(e);
   bdss_status st = finish(h, info);
   if (st != BDSS_OK) return st;
-  if (is_mixed(h)) {
-    uint64_t bits = h->hst->nrm[2];
-    memcpy(&h->normA, &bits, sizeof(double));
-  }
+  h->norm_valid = false;  // ||A||_inf comes with the first residual
   h->A_diag = A_diag;
   h->A_sub = A_sub;
   h->factored = true;
@@ -417,15 +411,21 @@ static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_i
   double berr = -1.0;
   for (int it = 0;; ++it) {
     cudaError_t e = reset_status(h);
+    const int with_norm = h->norm_valid ? 0 : 1;
     if (e == cudaSuccess)
-      e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst,
+      e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
                                           (int)std::min<long long>(h->N, 2LL * h->sms), h->stream)
-                   : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst,
+                   : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
                                      grid_for(h, h->N) * 2, h->stream);
     h->launches += 1;
     if (e != cudaSuccess) return cuda_fail(e);
     bdss_status st = finish(h, nullptr);
     if (st != BDSS_OK) return st;
+    if (with_norm) {
+      uint64_t bits = h->hst->nrm[2];
+      memcpy(&h->normA, &bits, sizeof(double));
+      h->norm_valid = true;
+    }
     double rn, xn;
     uint64_t b0 = h->hst->nrm[0], b1 = h->hst->nrm[1];
     memcpy(&rn, &b0, sizeof(double));

@@ -115,6 +115,23 @@ __device__ __forceinline__ void set_status(DevStatus *st, int code, long long le
   }
 }
 
+// CTA-wide maximum of a non-negative double, then one atomicMax on its bit
+// pattern (non-negative doubles order like their bit patterns).  All
+// threads call.
+__device__ inline void cta_max_to(unsigned long long *dst, double v) {
+  __shared__ double s_w[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_w[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, s_w[w]);
+    atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
 // Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
 // timeout_ns (or an iteration cap) the waiting CTA records BDSS_ERR_TIMEOUT
 // and returns false; any recorded error also makes it return false.  The
@@ -422,9 +439,8 @@ __device__ int chol_fused(T *s, int ld, int n, T *V1, int nv1, T *V2, int nv2, i
 // then all lanes update their rows.  One warp runs the whole solve, so the
 // FP64 work of a handful of vectors fills its lanes instead of one lane per
 // vector.  Call from exactly one warp.
-template <typename T>
+template <typename T, int C = 4>
 __device__ void trsv_fwd_warp(const T *sL, int ld, int n, T *V, int nv) {
-  constexpr int C = 4;
   const int lane = threadIdx.x & 31;
   for (int c0 = 0; c0 < nv; c0 += C) {
     const int cn = min(C, nv - c0);
@@ -469,9 +485,8 @@ __device__ void trsv_fwd_warp(const T *sL, int ld, int n, T *V, int nv) {
 }
 
 // L^T z = t, same organisation, from the last row up.
-template <typename T>
+template <typename T, int C = 4>
 __device__ void trsv_bwd_warp(const T *sL, int ld, int n, T *V, int nv) {
-  constexpr int C = 4;
   const int lane = threadIdx.x & 31;
   for (int c0 = 0; c0 < nv; c0 += C) {
     const int cn = min(C, nv - c0);
@@ -511,6 +526,22 @@ __device__ void trsv_bwd_warp(const T *sL, int ld, int n, T *V, int nv) {
       if (c < cn && lane + 32 < n) V[(c0 + c) * ld + lane + 32] = y1[c];
     }
   }
+}
+
+// The same substitutions with the vectors spread over the CTA's warps, one
+// vector per warp at a time: a warp issues at most one FP64 instruction per
+// ~64 cycles on this GPU, so a handful of right-hand sides on one warp is
+// bound by that rate while the SM's other FP64 units idle.  Same operations
+// per vector as above.  All threads call; no barrier inside.
+template <typename T>
+__device__ void trsv_fwd_cta(const T *sL, int ld, int n, T *V, int nv) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = warp; v < nv; v += nw) trsv_fwd_warp<T, 1>(sL, ld, n, V + (size_t)v * ld, 1);
+}
+template <typename T>
+__device__ void trsv_bwd_cta(const T *sL, int ld, int n, T *V, int nv) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = warp; v < nv; v += nw) trsv_bwd_warp<T, 1>(sL, ld, n, V + (size_t)v * ld, 1);
 }
 
 // Forward substitution L w = v for `nv` staged vectors (rows of V, stride
@@ -663,7 +694,6 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
   T *sL = smem;
   T *sV = sL + (size_t)n * ld;                          // up to n coupling vectors (one pass)
   T *sB = sV + (size_t)(factor ? n : 0) * ld;           // d RHS vectors
-  const int warp = threadIdx.x >> 5;
   const T *E = (l == 0) ? nullptr : a.Wb + (size_t)a.p.off[l] * nn;
   T *W = a.Wb + (size_t)a.p.off[l] * nn;
   const T *EL = (l == 0) ? nullptr : E + (size_t)(j - 1) * nn;
@@ -705,14 +735,14 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       bad = chol_fused(sL, ld, n, sV, 0, sB, 0, s_flag);
       if (!bad) {
         if (nvf > 0) trsv_fwd_rows(sL, ld, n, sV, nvf);
-        if (d > 0 && warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
+        if (d > 0) trsv_fwd_cta(sL, ld, n, sB, d);
         __syncthreads();
       }
     } else {
       bad = chol_staged(sL, ld, n, s_flag);
       if (!bad) {
         if (nvf > 0) trsv_fwd_rows(sL, ld, n, sV, nvf);
-        if (d > 0) trsv_fwd_warp(sL, ld, n, sB, d);
+        if (d > 0) trsv_fwd_cta(sL, ld, n, sB, d);
         __syncthreads();
       }
     }
@@ -729,7 +759,7 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       }
     }
   } else if (d > 0) {
-    if (warp == 0) trsv_fwd_warp(sL, ld, n, sB, d);
+    trsv_fwd_cta(sL, ld, n, sB, d);
     __syncthreads();
   }
   if (nvf > 0) {
@@ -992,10 +1022,13 @@ __device__ bool top_block(const Args<T> &a, bool factor, double *smem, int *s_fl
     }
   }
   if (d > 0) {
-    if (threadIdx.x < 32) {
-      trsv_fwd_warp(sL, ld, n, sB, d);
-      __syncwarp();
-      trsv_bwd_warp(sL, ld, n, sB, d);
+    {
+      const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int v = warp; v < d; v += nw) {
+        trsv_fwd_warp<double, 1>(sL, ld, n, sB + (size_t)v * ld, 1);
+        __syncwarp();
+        trsv_bwd_warp<double, 1>(sL, ld, n, sB + (size_t)v * ld, 1);
+      }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
@@ -1053,7 +1086,7 @@ __device__ void phaseC(const Args<T> &a, int l, long long j, T *smem) {
     sT[c * ld + q] = acc;
   }
   __syncthreads();
-  if (threadIdx.x < 32) trsv_bwd_warp(sL, ld, n, sT, d);
+  trsv_bwd_cta(sL, ld, n, sT, d);
   __syncthreads();
   T *Yo = a.Y + (size_t)orig * nd;
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {

@@ -97,23 +97,28 @@ __global__ void __launch_bounds__(kThreads) k_phaseC(const __grid_constant__ Arg
 // ---------------------------------------------------------------------------
 // FP64 residual of the refinement loop: R = B - A X, one CTA per block row.
 // sym(A_ii) is staged once in shared memory as S = A_ii + A_ii^T; every
-// thread then owns one (row r, column c) output:
-//   R[r][c] = B[r][c] - 0.5 (S x_i)[r][c] - (A_{i,i-1} x_{i-1})[r][c]
-//                                       - (A_{i+1,i}^T x_{i+1})[r][c]
-// with the two coupling blocks read through L1.  Also the max-norms
-// ||R||_inf and ||X||_inf (max over rows of absolute row sums), accumulated
-// with atomicMax on the bit patterns of non-negative doubles, which order
-// like the values.  R is written in FP32 for the FP32 correction solve.
+// thread then owns one (row r, column c) output
+//   R[r][c] = B[r][c] - ((A_{i,i-1} x_{i-1})[r][c] + (A_{i+1,i}^T x_{i+1})[r][c])
+//                     - 0.5 (S x_i)[r][c]
+// with the three products accumulated as independent chains (the coupling
+// blocks read through L1; a missing neighbour multiplies zeros).  Also the
+// max-norms ||R||_inf and ||X||_inf (max over rows of absolute row sums),
+// reduced in the CTA and merged with one atomicMax per CTA.  R is written in
+// FP32 for the FP32 correction solve.  With with_norm, also ||A||_inf from
+// the same reads (row r sums |sym(A_ii)[r][:]|, |A_{i,i-1}[r][:]| and
+// |A_{i+1,i}[:][r]|), in FP32 arithmetic: it only scales the refinement's
+// stopping test, where a relative error of 1e-6 is immaterial.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d, const double *A_diag,
                                                        const double *A_sub, const double *X, const double *B,
-                                                       float *R32, DevStatus *st) {
+                                                       float *R32, DevStatus *st, int with_norm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ld = ldstride(n);
   double *sS = reinterpret_cast<double *>(smem_raw);  // A_ii + A_ii^T
   double *sX = sS + (size_t)n * ld;                     // x_{i-1}, x_i, x_{i+1}: [3][n][d]
-  double *sR = sX + (size_t)3 * n * d;                  // row sums |R|, |x_i|: [2][n]
+  double *sA = sX + (size_t)3 * n * d;                  // |R| entries: [n][d]
   const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  double maxR = 0.0, maxX = 0.0, maxA = 0.0;
   for (long long i = blockIdx.x; i < N; i += gridDim.x) {
     stage_rows(sS, ld, A_diag + i * nn, n);
     for (int e = threadIdx.x; e < 3 * n * d; e += blockDim.x) {
@@ -121,7 +126,6 @@ __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d
       const long long blk = i - 1 + w;
       sX[e] = (blk >= 0 && blk < N) ? ldcg(X + blk * nd + rem) : 0.0;
     }
-    for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) sR[e] = 0.0;
     __syncthreads();
     // S = A + A^T in place: each unordered pair (r, p) belongs to one thread
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -134,67 +138,55 @@ __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d
     }
     __syncthreads();
     const double *xm = sX, *x0 = sX + nd, *xp = sX + 2 * nd;
-    const double *Al = A_sub + (i - 1) * nn;  // A_{i,i-1} (valid when i > 0)
-    const double *Au = A_sub + i * nn;        // A_{i+1,i} (valid when i + 1 < N)
+    // missing neighbours: any valid finite block times the zero x staged above
+    const double *Al = i > 0 ? A_sub + (i - 1) * nn : A_diag;  // A_{i,i-1}
+    const double *Au = i + 1 < N ? A_sub + i * nn : A_diag;    // A_{i+1,i}
     for (int t = threadIdx.x; t < n * d; t += blockDim.x) {
       const int r = t / d, c = t - r * d;
-      double accD = 0.0, acc = 0.0;
+      double accD = 0.0, accL = 0.0, accU = 0.0;
       const double *Sr = sS + r * ld;
-      for (int p = 0; p < n; ++p) accD = fma(Sr[p], x0[p * d + c], accD);
-      if (i > 0)
-        for (int p = 0; p < n; ++p) acc = fma(__ldg(Al + (size_t)r * n + p), xm[p * d + c], acc);
-      if (i + 1 < N)
-        for (int p = 0; p < n; ++p) acc = fma(__ldg(Au + (size_t)p * n + r), xp[p * d + c], acc);
-      const double rv = (ldcg(B + i * nd + t) - acc) - 0.5 * accD;
+      const double *Alr = Al + (size_t)r * n, *Aur = Au + r;
+      if (with_norm) {  // uniform over the launch: no divergence
+        const bool hl = i > 0, hu = i + 1 < N;
+        float na = 0.0f;
+#pragma unroll 4
+        for (int p = 0; p < n; ++p) {
+          const double s_ = Sr[p], l_ = __ldg(Alr + p), u_ = __ldg(Aur + (size_t)p * n);
+          accD = fma(s_, x0[p * d + c], accD);
+          accL = fma(l_, xm[p * d + c], accL);
+          accU = fma(u_, xp[p * d + c], accU);
+          na += 0.5f * fabsf((float)s_) + (hl ? fabsf((float)l_) : 0.0f) + (hu ? fabsf((float)u_) : 0.0f);
+        }
+        maxA = fmax(maxA, (double)na);
+      } else {
+#pragma unroll 4
+        for (int p = 0; p < n; ++p) {
+          accD = fma(Sr[p], x0[p * d + c], accD);
+          accL = fma(__ldg(Alr + p), xm[p * d + c], accL);
+          accU = fma(__ldg(Aur + (size_t)p * n), xp[p * d + c], accU);
+        }
+      }
+      const double rv = (ldcg(B + i * nd + t) - (accL + accU)) - 0.5 * accD;
       R32[i * nd + t] = (float)rv;
-      atomicAdd(&sR[r], fabs(rv));
-      atomicAdd(&sR[n + r], fabs(x0[t]));
+      sA[t] = fabs(rv);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      atomicMax(&st->nrm[0], (unsigned long long)__double_as_longlong(sR[r]));
-      atomicMax(&st->nrm[1], (unsigned long long)__double_as_longlong(sR[n + r]));
+      double rs = 0.0, xs = 0.0;
+      for (int c = 0; c < d; ++c) {
+        rs += sA[r * d + c];
+        xs += fabs(x0[r * d + c]);
+      }
+      maxR = fmax(maxR, rs);
+      maxX = fmax(maxX, xs);
     }
     __syncthreads();
   }
+  cta_max_to(&st->nrm[0], maxR);
+  cta_max_to(&st->nrm[1], maxX);
+  if (with_norm) cta_max_to(&st->nrm[2], maxA);
 }
 
-// ||A||_inf of the full operator, in FP32 arithmetic (it only scales the
-// refinement's stopping test, where a relative error of 1e-6 is immaterial,
-// and FP32 adds are ~60x cheaper than FP64 ones here): one CTA per block row,
-// each row's absolute sum split over kNormSplit threads and combined in
-// shared memory; the row maxima are stored as FP64 bit patterns.
-constexpr int kNormSplit = 4;
-
-__global__ void __launch_bounds__(kThreads) k_norm_A(long long N, int n, const double *A_diag,
-                                                     const double *A_sub, DevStatus *st) {
-  __shared__ float rs[kThreads];
-  const size_t nn = (size_t)n * n;
-  for (long long i = blockIdx.x; i < N; i += gridDim.x) {
-    for (int r = threadIdx.x; r < n; r += blockDim.x) rs[r] = 0.0f;
-    __syncthreads();
-    for (int t = threadIdx.x; t < n * kNormSplit; t += blockDim.x) {
-      const int r = t / kNormSplit, q = t - r * kNormSplit;
-      float s = 0.0f, sd = 0.0f;
-      const double *D = A_diag + i * nn;
-      for (int p = q; p < n; p += kNormSplit)
-        sd += fabsf((float)__ldg(D + (size_t)r * n + p) + (float)__ldg(D + (size_t)p * n + r));
-      if (i > 0) {
-        const double *S = A_sub + (i - 1) * nn;
-        for (int p = q; p < n; p += kNormSplit) s += fabsf((float)__ldg(S + (size_t)r * n + p));
-      }
-      if (i + 1 < N) {
-        const double *S = A_sub + i * nn;
-        for (int p = q; p < n; p += kNormSplit) s += fabsf((float)__ldg(S + (size_t)p * n + r));
-      }
-      atomicAdd(&rs[r], fmaf(0.5f, sd, s));
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x)
-      atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong((double)rs[r]));
-    __syncthreads();
-  }
-}
 
 // log det: sum over eliminated blocks (every original block i >= 1) of
 // -2 sum_k log(1/L_kk) plus the top block's; reduced per CTA into out[blockIdx].
@@ -353,17 +345,12 @@ cudaError_t launch_phaseC(const Args<T> &a, int l, int grid, size_t smem, cudaSt
 }
 
 cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
-                            const double *B, float *R32, DevStatus *st, int grid, cudaStream_t s) {
-  const size_t sm = ((size_t)n * ldstride(n) + (size_t)3 * n * d + (size_t)2 * n) * sizeof(double);
-  k_residual<<<grid, kThreads, sm, s>>>(N, n, d, A_diag, A_sub, X, B, R32, st);
+                            const double *B, float *R32, DevStatus *st, int with_norm, int grid, cudaStream_t s) {
+  const size_t sm = ((size_t)n * ldstride(n) + (size_t)3 * n * d + (size_t)n * d) * sizeof(double);
+  k_residual<<<grid, kThreads, sm, s>>>(N, n, d, A_diag, A_sub, X, B, R32, st, with_norm);
   return cudaGetLastError();
 }
 
-cudaError_t launch_norm_A(long long N, int n, const double *A_diag, const double *A_sub, DevStatus *st, int grid,
-                          cudaStream_t s) {
-  k_norm_A<<<grid, kThreads, 0, s>>>(N, n, A_diag, A_sub, st);
-  return cudaGetLastError();
-}
 
 template <typename T>
 cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, double *partial, int grid,

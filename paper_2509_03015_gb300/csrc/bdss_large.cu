@@ -127,10 +127,11 @@ constexpr int kResCols = 16;
 
 __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, int d, const double *A_diag,
                                                             const double *A_sub, const double *X, const double *B,
-                                                            float *R32, DevStatus *st) {
+                                                            float *R32, DevStatus *st, int with_norm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *sX = reinterpret_cast<double *>(smem_raw);  // x_{i-1}, x_i, x_{i+1}: [3][n][d]
   const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  double maxR = 0.0, maxX = 0.0, maxA = 0.0;
   for (long long i = blockIdx.x; i < N; i += gridDim.x) {
     for (int e = threadIdx.x; e < 3 * n * d; e += blockDim.x) {
       const int w = e / (n * d), rem = e - w * n * d;
@@ -142,13 +143,16 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
     const double *D = A_diag + i * nn;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
       double rs = 0.0, xs = 0.0;
+      float na = 0.0f;  // ||A||_inf row sum (with_norm), FP32 as it only scales the stop test
       for (int c0 = 0; c0 < d; c0 += kResCols) {
+        const bool nrm = with_norm && c0 == 0;
         const int dc = min(kResCols, d - c0);
         double accD[kResCols], acc[kResCols];
 #pragma unroll
         for (int c = 0; c < kResCols; ++c) accD[c] = acc[c] = 0.0;
         for (int p = 0; p < n; ++p) {
           const double sp = __ldg(D + (size_t)r * n + p) + __ldg(D + (size_t)p * n + r);
+          if (nrm) na += 0.5f * fabsf((float)sp);
 #pragma unroll
           for (int c = 0; c < kResCols; ++c)
             if (c < dc) accD[c] = fma(sp, x0[p * d + c0 + c], accD[c]);
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
           const double *Al = A_sub + (i - 1) * nn;
           for (int p = 0; p < n; ++p) {
             const double v = __ldg(Al + (size_t)r * n + p);
+            if (nrm) na += fabsf((float)v);
 #pragma unroll
             for (int c = 0; c < kResCols; ++c)
               if (c < dc) acc[c] = fma(v, xm[p * d + c0 + c], acc[c]);
@@ -166,6 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
           const double *Au = A_sub + i * nn;
           for (int p = 0; p < n; ++p) {
             const double v = __ldg(Au + (size_t)p * n + r);
+            if (nrm) na += fabsf((float)v);
 #pragma unroll
             for (int c = 0; c < kResCols; ++c)
               if (c < dc) acc[c] = fma(v, xp[p * d + c0 + c], acc[c]);
@@ -181,11 +187,15 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
             xs += fabs(x0[r * d + c0 + c]);
           }
       }
-      atomicMax(&st->nrm[0], (unsigned long long)__double_as_longlong(rs));
-      atomicMax(&st->nrm[1], (unsigned long long)__double_as_longlong(xs));
+      maxR = fmax(maxR, rs);
+      maxX = fmax(maxX, xs);
+      maxA = fmax(maxA, (double)na);
     }
     __syncthreads();
   }
+  cta_max_to(&st->nrm[0], maxR);
+  cta_max_to(&st->nrm[1], maxX);
+  if (with_norm) cta_max_to(&st->nrm[2], maxA);
 }
 
 __global__ void k_tc_selftest(const __grid_constant__ CUtensorMap map, const float *W, int n, double *err,
@@ -366,10 +376,10 @@ cudaError_t run_tc_selftest(double *max_err, int *status) {
 }
 
 cudaError_t launch_residual_rows(long long N, int n, int d, const double *A_diag, const double *A_sub,
-                                 const double *X, const double *B, float *R32, DevStatus *st, int grid,
-                                 cudaStream_t s) {
+                                 const double *X, const double *B, float *R32, DevStatus *st, int with_norm,
+                                 int grid, cudaStream_t s) {
   const size_t sm = (size_t)3 * n * d * sizeof(double);
-  k_residual_rows<<<grid, kThreads, sm, s>>>(N, n, d, A_diag, A_sub, X, B, R32, st);
+  k_residual_rows<<<grid, kThreads, sm, s>>>(N, n, d, A_diag, A_sub, X, B, R32, st, with_norm);
   return cudaGetLastError();
 }
 

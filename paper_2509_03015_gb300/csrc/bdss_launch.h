@@ -21,11 +21,9 @@ template <typename T>
 cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, double *partial, int grid,
                           cudaStream_t s);
 cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
-                            const double *B, float *R32, DevStatus *st, int grid, cudaStream_t s);
+                            const double *B, float *R32, DevStatus *st, int with_norm, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, const double *X, double *dA_diag,
                                  double *dA_sub, int grid, cudaStream_t s);
-cudaError_t launch_norm_A(long long N, int n, const double *A_diag, const double *A_sub, DevStatus *st, int grid,
-                          cudaStream_t s);
 
 // large-block path (64 < n <= 256)
 constexpr int kMaxNLarge = 256;
@@ -40,7 +38,7 @@ long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int 
 cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows, int n);
 cudaError_t run_tc_selftest(double *max_err, int *status);
 cudaError_t launch_residual_rows(long long N, int n, int d, const double *A_diag, const double *A_sub,
-                                 const double *X, const double *B, float *R32, DevStatus *st, int grid,
-                                 cudaStream_t s);
+                                 const double *X, const double *B, float *R32, DevStatus *st, int with_norm,
+                                 int grid, cudaStream_t s);
 
 }  // namespace bdss
