@@ -115,6 +115,19 @@ __device__ __forceinline__ void set_status(DevStatus *st, int code, long long le
   }
 }
 
+// |x| as an FP32 value built from the IEEE-754 fields of the FP64 x with
+// integer operations only: the exponent is rebiased (1023 -> 127) and the
+// top 20 of the 52 fraction bits are kept, so the relative error is below
+// 2^-20; magnitudes below 2^-126 give 0 and from 2^128 up (and NaN) give
+// +inf.  Used for norm estimates, where a conversion instruction would
+// occupy the narrow FP64 pipe.
+__device__ __forceinline__ float abs_f32_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x) & 0x7FFFFFFFu;  // exponent and fraction[51:32]
+  if (hi < (897u << 20)) return 0.0f;
+  if (hi >= (1151u << 20)) return __int_as_float(0x7F800000);
+  return __uint_as_float((hi - (896u << 20)) << 3);
+}
+
 // CTA-wide maximum of a non-negative double, then one atomicMax on its bit
 // pattern (non-negative doubles order like their bit patterns).  All
 // threads call.

@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(kThreads) k_phaseC(const __grid_constant__ Arg
 // reduced in the CTA and merged with one atomicMax per CTA.  R is written in
 // FP32 for the FP32 correction solve.  With with_norm, also ||A||_inf from
 // the same reads (row r sums |sym(A_ii)[r][:]|, |A_{i,i-1}[r][:]| and
-// |A_{i+1,i}[:][r]|), in FP32 arithmetic: it only scales the refinement's
-// stopping test, where a relative error of 1e-6 is immaterial.
+// |A_{i+1,i}[:][r]|), in FP32 arithmetic on magnitudes taken from the FP64
+// bit fields (abs_f32_bits): it only scales the refinement's stopping test,
+// where a relative error of 1e-6 is immaterial.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d, const double *A_diag,
                                                        const double *A_sub, const double *X, const double *B,
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d
           accD = fma(s_, x0[p * d + c], accD);
           accL = fma(l_, xm[p * d + c], accL);
           accU = fma(u_, xp[p * d + c], accU);
-          na += 0.5f * fabsf((float)s_) + (hl ? fabsf((float)l_) : 0.0f) + (hu ? fabsf((float)u_) : 0.0f);
+          na += 0.5f * abs_f32_bits(s_) + (hl ? abs_f32_bits(l_) : 0.0f) + (hu ? abs_f32_bits(u_) : 0.0f);
         }
         maxA = fmax(maxA, (double)na);
       } else {

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
         for (int c = 0; c < kResCols; ++c) accD[c] = acc[c] = 0.0;
         for (int p = 0; p < n; ++p) {
           const double sp = __ldg(D + (size_t)r * n + p) + __ldg(D + (size_t)p * n + r);
-          if (nrm) na += 0.5f * fabsf((float)sp);
+          if (nrm) na += 0.5f * abs_f32_bits(sp);
 #pragma unroll
           for (int c = 0; c < kResCols; ++c)
             if (c < dc) accD[c] = fma(sp, x0[p * d + c0 + c], accD[c]);
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
           const double *Al = A_sub + (i - 1) * nn;
           for (int p = 0; p < n; ++p) {
             const double v = __ldg(Al + (size_t)r * n + p);
-            if (nrm) na += fabsf((float)v);
+            if (nrm) na += abs_f32_bits(v);
 #pragma unroll
             for (int c = 0; c < kResCols; ++c)
               if (c < dc) acc[c] = fma(v, xm[p * d + c0 + c], acc[c]);
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_rows(long long N, int n, 
           const double *Au = A_sub + i * nn;
           for (int p = 0; p < n; ++p) {
             const double v = __ldg(Au + (size_t)p * n + r);
-            if (nrm) na += fabsf((float)v);
+            if (nrm) na += abs_f32_bits(v);
 #pragma unroll
             for (int c = 0; c < kResCols; ++c)
               if (c < dc) acc[c] = fma(v, xp[p * d + c0 + c], acc[c]);

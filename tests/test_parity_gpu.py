@@ -249,3 +249,29 @@ def test_fp32_ir_kalman_N16384_n64(oracle_mod):
     Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
     assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+
+
+@pytest.mark.parametrize("N,n,d", [(300, 64, 2), (65, 160, 3)])
+def test_reported_backward_error_matches_oracle(oracle_mod, N, n, d):
+    # max_refine = 0: the library stops after its first residual and reports
+    # ||B - A X||_inf / (||A||_inf ||X||_inf) of the FP32 solution (~1e-7),
+    # with ||A||_inf estimated from FP64 bit fields; at that size the plain
+    # FP64 residual is exact to many digits, so the report must agree with
+    # the oracle's compensated value to well within the 2^-20 norm estimate
+    from paper_2509_03015_gb300 import Solver
+    from paper_2509_03015_gb300._lib import BDSSError
+    s = inputs.random_btd(N, n, d, seed=5 + N)
+    Ad, As, B = _dev(s)
+    solver = Solver(N, n, d_max=d, precision="fp32_ir")
+    try:
+        solver.set_option("max_refine", 0)
+        with pytest.raises(BDSSError) as e:
+            X = torch.empty_like(B)
+            solver.factor_solve(Ad, As, B, X)
+        assert e.value.status == 7  # NO_CONVERGENCE after zero corrections
+        reported = e.value.info.backward_err
+        ref = oracle_mod.backward_error(s["A_diag"], s["A_sub"], X.cpu().numpy(), s["B"])
+        assert 1e-12 < ref < 1e-3
+        assert abs(reported - ref) <= 1e-5 * ref
+    finally:
+        solver.close()
