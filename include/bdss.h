@@ -15,7 +15,18 @@
  *            sym(A_{i,i}) = (A_{i,i} + A_{i,i}^T) / 2.
  *   A_sub  : (N-1) x n x n doubles, A_sub[i] = A_{i+1,i}.  May be NULL iff N == 1.
  *   B, X   : N x n x d doubles, element (i, r, k) at ((i n + r) d + k).
- * Every device pointer must be 16-byte aligned.
+ * Every pointer must be 16-byte aligned.
+ *
+ * Input location.  A_diag, A_sub and B may also be host memory that the GPU
+ * can read: page-locked memory (cudaHostAlloc, cudaHostRegister) or, on a
+ * system whose GPU reads pageable host memory (cudaDevAttrPageableMemoryAccess,
+ * e.g. a coherent NVLink-C2C host link), any host memory.  The level-0
+ * kernels then read the inputs in place, asking L2 for the next task's blocks
+ * one task ahead, so that the transfer overlaps the factorisation; the FP64
+ * path reads every input element once per bdss_factor_solve.  The mixed modes
+ * read A again for every refinement residual, where device copies are
+ * faster.  X must be device (or managed) memory.  A pointer the GPU cannot
+ * read is rejected with BDSS_ERR_INVALID_ARG before any launch.
  *
  * Ownership.  The caller owns every input and output buffer; the library never
  * frees them.  A handle owns its workspace (factors of every level, the
@@ -90,10 +101,12 @@ typedef enum {
 } bdss_option;
 
 /*
- * Create a solver for systems with N >= 1 blocks of size 1 <= n <= 64 and up
- * to d_max >= 1 right-hand-side columns, allocating all device workspace
- * (the "Init" phase of the evaluation in Sec. 4.2).  `cuda_stream` is a
- * cudaStream_t (NULL = default stream).  On success *h is a new handle.
+ * Create a solver for systems with N >= 1 blocks of size 1 <= n <= 256 and
+ * 1 <= d_max <= 64 right-hand-side columns, allocating all device workspace
+ * (the "Init" phase of the evaluation in Sec. 4.2).  Blocks up to n = 64 are
+ * staged whole in one CTA's shared memory; 64 < n <= 256 runs the tiled path
+ * (64 x 64 tiles).  `cuda_stream` is a cudaStream_t (NULL = default stream).
+ * On success *h is a new handle; n > 256 gives BDSS_ERR_UNSUPPORTED.
  */
 bdss_status bdss_create(bdss_handle *h, int64_t N, int32_t n, int32_t d_max,
                         bdss_precision prec, void *cuda_stream);

@@ -340,15 +340,52 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
   return BDSS_ERR_INVALID_ARG;
 }
 
+// Can the device read p in place?  Device and managed memory; page-locked
+// host memory mapped at the same address (unified addressing); other host
+// memory only where the device reads pageable memory.
+static bool device_readable(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+      return true;
+    case cudaMemoryTypeHost:
+      return at.devicePointer == p;
+    default: {
+      int dev = 0, pageable = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      return pageable != 0;
+    }
+  }
+}
+
+static bool device_memory(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 static bdss_status check_factor_args(bdss_ctx *h, const double *A_diag, const double *A_sub) {
-  if (!A_diag || !aligned16(A_diag)) return BDSS_ERR_INVALID_ARG;
-  if (h->N > 1 && (!A_sub || !aligned16(A_sub))) return BDSS_ERR_INVALID_ARG;
+  if (!A_diag || !aligned16(A_diag) || !device_readable(A_diag)) return BDSS_ERR_INVALID_ARG;
+  if (h->N > 1 && (!A_sub || !aligned16(A_sub) || !device_readable(A_sub))) return BDSS_ERR_INVALID_ARG;
   return BDSS_OK;
 }
 
 static bdss_status check_solve_args(bdss_ctx *h, const double *B, double *X, int d) {
   if (!B || !X || !aligned16(B) || !aligned16(X)) return BDSS_ERR_INVALID_ARG;
   if (d < 1 || d > h->d_max) return BDSS_ERR_INVALID_ARG;
+  if (!device_readable(B) || !device_memory(X)) return BDSS_ERR_INVALID_ARG;
   return BDSS_OK;
 }
 

@@ -145,6 +145,16 @@ __device__ inline void cta_max_to(unsigned long long *dst, double v) {
   }
 }
 
+// Ask L2 for `bytes` starting at p (prefetch.global.L2, one 128-byte line
+// per thread and step).  Used one task ahead on the caller's level-0 inputs,
+// so that blocks held in host memory cross the link while the CTA works on
+// its current block.  All threads call.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const char *c = static_cast<const char *>(p);
+  for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
+}
+
 // Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
 // timeout_ns (or an iteration cap) the waiting CTA records BDSS_ERR_TIMEOUT
 // and returns false; any recorded error also makes it return false.  The
@@ -227,12 +237,21 @@ static __device__ __noinline__ int spread_rank(DevStatus *st, long long timeout_
 // Staging helpers (all threads of the CTA participate).
 // ---------------------------------------------------------------------------
 
-// s[i*ld + c] = sym(A)[i][c] for c <= i, from a caller FP64 block.
+// s[i*ld + c] = sym(A)[i][c] = (A[i][c] + A[c][i]) / 2 for c <= i, from a
+// caller FP64 block: the whole block is staged row by row (reads in address
+// order, also over a host link), then the lower triangle is symmetrised in
+// shared memory (the upper triangle is left holding A).  Contains a barrier:
+// all threads call.
 template <typename T>
 __device__ void stage_sym_lower(T *s, int ld, const double *g, int n) {
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, c = e - i * n;
-    if (c <= i) s[i * ld + c] = T(0.5) * ((T)ldcg(g + i * n + c) + (T)ldcg(g + c * n + i));
+    s[i * ld + c] = (T)ldcg(g + e);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, c = e - i * n;
+    if (c < i) s[i * ld + c] = T(0.5) * (s[i * ld + c] + s[c * ld + i]);
   }
 }
 // s[i*ld + c] = g[i][c] for c <= i (lower triangle of a workspace block).
@@ -641,6 +660,12 @@ __host__ __device__ inline size_t smem_top_bytes(int n, int d) {
   return ((size_t)n * ld + (size_t)d * ld + 8) * sizeof(double);
 }
 
+// The FP32 path (n <= 64) keeps L^{-1} instead of L in the slot of every
+// eliminated block, so that its solve passes (run once per refinement step)
+// apply the triangular factors as products instead of substitutions; the
+// extra n^3/6 FMAs per block are FP32.  The diagonal still holds 1 / L_kk.
+template <typename T> constexpr bool kStoreInverse = sizeof(T) == 4;
+
 // CTAs per block at a level with few blocks: the persistent grid holds
 // `capacity` CTAs; when a level has fewer blocks than that, each block's
 // work is split over up to max_parts CTAs (one CTA per block would leave most
@@ -677,6 +702,22 @@ __device__ void stage_row_range(T *s, int ld, const S *g, int n, int r0, int r1)
     const int r = e / n, c = e - r * n;
     s[r * ld + c] = (T)ldcg(g + (size_t)(r0 + r) * n + c);
   }
+}
+
+// Level-0 inputs of eliminated position j (A_jj, A_{j,j-1}, A_{j+1,j}, b_j)
+// and of separator position s (A_ss, b_s), for prefetch_l2.
+template <typename T>
+__device__ void prefetch_elim_inputs(const Args<T> &a, long long j) {
+  const size_t nn = (size_t)a.p.n * a.p.n, nd = (size_t)a.p.n * a.d;
+  prefetch_l2(a.A_diag + j * nn, nn * sizeof(double));
+  prefetch_l2(a.A_sub + (j - 1) * nn, (j + 1 < a.p.N ? 2 : 1) * nn * sizeof(double));
+  if (a.B64 && nd) prefetch_l2(a.B64 + j * nd, nd * sizeof(double));
+}
+template <typename T>
+__device__ void prefetch_sep_inputs(const Args<T> &a, long long s) {
+  const size_t nn = (size_t)a.p.n * a.p.n, nd = (size_t)a.p.n * a.d;
+  prefetch_l2(a.A_diag + s * nn, nn * sizeof(double));
+  if (a.B64 && nd) prefetch_l2(a.B64 + s * nd, nd * sizeof(double));
 }
 
 // ---------------------------------------------------------------------------
@@ -764,13 +805,25 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
       __syncthreads();
       return false;
     }
-    if (part == 0) {
+    if (part == 0 && !kStoreInverse<T>) {
       T *Lg = a.Ld + orig * nn;
       for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int r = e / n, c = e - r * n;
         if (c <= r) Lg[e] = sL[r * ld + c];
       }
     }
+  } else if (d > 0 && kStoreInverse<T>) {
+    // FP32 solve pass: y = L^{-1} b as a product with the stored inverse
+    T *Yj = a.Y + (size_t)orig * n * d;
+    for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+      const int i = e / d, c = e - i * d;
+      const T *li = sL + i * ld, *b = sB + c * ld;
+      T acc = T(0);
+      for (int p = 0; p <= i; ++p) acc = fma(li[p], b[p], acc);
+      Yj[e] = acc;
+    }
+    __syncthreads();
+    return true;
   } else if (d > 0) {
     trsv_fwd_cta(sL, ld, n, sB, d);
     __syncthreads();
@@ -802,6 +855,22 @@ __device__ bool phaseA(const Args<T> &a, int l, long long j, bool factor, T *sme
     for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
       const int c = e / n, i = e - c * n;
       WR[(size_t)(r0 + c) * n + i] = sV[c * ld + i];
+    }
+  }
+  if (kStoreInverse<T> && factor && part == 0) {
+    // FP32: store L^{-1} (its diagonal is the same 1 / L_kk): the columns of
+    // the identity through the substitution
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int c = e / n, i = e - c * n;
+      sV[c * ld + i] = (i == c) ? T(1) : T(0);
+    }
+    __syncthreads();
+    trsv_fwd_rows(sL, ld, n, sV, n);
+    T *Lg = a.Ld + orig * nn;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, c = e - i * n;
+      if (c <= i) Lg[e] = sV[c * ld + i];
     }
   }
   __syncthreads();
@@ -1099,12 +1168,22 @@ __device__ void phaseC(const Args<T> &a, int l, long long j, T *smem) {
     sT[c * ld + q] = acc;
   }
   __syncthreads();
-  trsv_bwd_cta(sL, ld, n, sT, d);
-  __syncthreads();
+  if (!kStoreInverse<T>) {
+    trsv_bwd_cta(sL, ld, n, sT, d);
+    __syncthreads();
+  }
   T *Yo = a.Y + (size_t)orig * nd;
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
     const int i = e / d, c = e - i * d;
-    const T x = sT[c * ld + i];
+    T x;
+    if (kStoreInverse<T>) {  // x = L^{-T} t with the stored inverse
+      const T *t = sT + c * ld;
+      T acc = T(0);
+      for (int k = i; k < n; ++k) acc = fma(sL[k * ld + i], t[k], acc);
+      x = acc;
+    } else {
+      x = sT[c * ld + i];
+    }
     Yo[e] = x;
     if (a.X64) {
       double *xo = a.X64 + (size_t)orig * nd + e;

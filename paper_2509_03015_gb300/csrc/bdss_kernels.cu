@@ -33,11 +33,16 @@ __global__ void __launch_bounds__(kThreads, PersistentOcc<T>::value)
     // task t -> block t % count, part t / count: the parts of one block sit
     // `count` ranks apart, i.e. on different SMs
     const int pA = parts_A<T>(a.p, l, factor, a.capacity);
-    for (long long t = rank; t < nElim * pA; t += gridDim.x)
+    for (long long t = rank; t < nElim * pA; t += gridDim.x) {
+      if (l == 0 && factor && t + gridDim.x < nElim * pA) prefetch_elim_inputs(a, 2 * ((t + gridDim.x) % nElim) + 1);
       if (!phaseA(a, l, 2 * (t % nElim) + 1, factor, smem, &s_flag, (int)(t / nElim), pA)) break;
+    }
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
     const int pB = parts_B<T>(a.p, l, factor, a.capacity);
-    for (long long t = rank; t < nSep * pB; t += gridDim.x) phaseB(a, l, t % nSep, factor, smem, (int)(t / nSep), pB);
+    for (long long t = rank; t < nSep * pB; t += gridDim.x) {
+      if (l == 0 && factor && t + gridDim.x < nSep * pB) prefetch_sep_inputs(a, 2 * ((t + gridDim.x) % nSep));
+      phaseB(a, l, t % nSep, factor, smem, (int)(t / nSep), pB);
+    }
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
   if (rank == 0) top_block(a, factor, reinterpret_cast<double *>(smem_raw), &s_flag);
@@ -61,10 +66,12 @@ __global__ void __launch_bounds__(kThreads) k_phaseA(const __grid_constant__ Arg
   if (status_set(a.st)) return;
   const long long nElim = a.p.Nl[l] / 2;
   const int pA = parts_A<T>(a.p, l, factor != 0, a.capacity);
-  for (long long t = blockIdx.x; t < nElim * pA; t += gridDim.x)
+  for (long long t = blockIdx.x; t < nElim * pA; t += gridDim.x) {
+    if (l == 0 && factor && t + gridDim.x < nElim * pA) prefetch_elim_inputs(a, 2 * ((t + gridDim.x) % nElim) + 1);
     if (!phaseA(a, l, 2 * (t % nElim) + 1, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, (int)(t / nElim),
                 pA))
       return;
+  }
 }
 
 template <typename T>
@@ -73,8 +80,10 @@ __global__ void __launch_bounds__(kThreads) k_phaseB(const __grid_constant__ Arg
   if (status_set(a.st)) return;
   const long long nSep = (a.p.Nl[l] + 1) / 2;
   const int pB = parts_B<T>(a.p, l, factor != 0, a.capacity);
-  for (long long t = blockIdx.x; t < nSep * pB; t += gridDim.x)
+  for (long long t = blockIdx.x; t < nSep * pB; t += gridDim.x) {
+    if (l == 0 && factor && t + gridDim.x < nSep * pB) prefetch_sep_inputs(a, 2 * ((t + gridDim.x) % nSep));
     phaseB(a, l, t % nSep, factor != 0, reinterpret_cast<T *>(smem_raw), (int)(t / nSep), pB);
+  }
 }
 
 template <typename T>

@@ -14,11 +14,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(None)
 
 
-def _check_tensor(t, name, shape=None):
+def _check_tensor(t, name, shape=None, host_ok=False):
+    """float64, contiguous, on the GPU -- or, for inputs (host_ok), in
+    page-locked host memory, which the kernels read in place."""
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    if t.device.type != "cuda" or t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    on_host = host_ok and t.device.type == "cpu" and t.is_pinned()
+    if (t.device.type != "cuda" and not on_host) or t.dtype != torch.float64 or not t.is_contiguous():
+        where = "CUDA or pinned host" if host_ok else "CUDA"
+        raise ValueError(f"{name} must be a contiguous float64 {where} tensor")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
@@ -51,9 +55,9 @@ class Solver:
 
     def factor(self, A_diag, A_sub):
         sd, ss, _ = self._shapes(1)
-        _check_tensor(A_diag, "A_diag", sd)
+        _check_tensor(A_diag, "A_diag", sd, host_ok=True)
         if self.N > 1:
-            _check_tensor(A_sub, "A_sub", ss)
+            _check_tensor(A_sub, "A_sub", ss, host_ok=True)
         info = _lib.bdss_info()
         st = self.lib.bdss_factor(self.h, _ptr(A_diag), _ptr(A_sub if self.N > 1 else None), ctypes.byref(info))
         _lib.check(st, "bdss_factor", info)
@@ -61,12 +65,12 @@ class Solver:
         return info
 
     def solve(self, B, X=None):
-        _check_tensor(B, "B")
+        _check_tensor(B, "B", host_ok=True)
         d = B.shape[-1]
         _, _, sb = self._shapes(d)
-        _check_tensor(B, "B", sb)
+        _check_tensor(B, "B", sb, host_ok=True)
         if X is None:
-            X = torch.empty_like(B)
+            X = torch.empty(B.shape, dtype=B.dtype, device="cuda")
         _check_tensor(X, "X", sb)
         info = _lib.bdss_info()
         st = self.lib.bdss_solve(self.h, _ptr(B), _ptr(X), d, ctypes.byref(info))
@@ -76,13 +80,13 @@ class Solver:
 
     def factor_solve(self, A_diag, A_sub, B, X=None):
         sd, ss, _ = self._shapes(1)
-        _check_tensor(A_diag, "A_diag", sd)
+        _check_tensor(A_diag, "A_diag", sd, host_ok=True)
         if self.N > 1:
-            _check_tensor(A_sub, "A_sub", ss)
+            _check_tensor(A_sub, "A_sub", ss, host_ok=True)
         d = B.shape[-1]
-        _check_tensor(B, "B", self._shapes(d)[2])
+        _check_tensor(B, "B", self._shapes(d)[2], host_ok=True)
         if X is None:
-            X = torch.empty_like(B)
+            X = torch.empty(B.shape, dtype=B.dtype, device="cuda")
         _check_tensor(X, "X", self._shapes(d)[2])
         info = _lib.bdss_info()
         st = self.lib.bdss_factor_solve(self.h, _ptr(A_diag), _ptr(A_sub if self.N > 1 else None), _ptr(B),

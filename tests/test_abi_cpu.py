@@ -82,3 +82,17 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load()
+
+
+def test_binding_rejects_pageable_host_tensors():
+    # inputs may be CUDA or pinned host tensors (read in place by the
+    # kernels); a pageable CPU tensor or a CPU output is refused up front
+    import torch
+    from paper_2509_03015_gb300.solver import _check_tensor
+    t = torch.zeros(2, 3, 3, dtype=torch.float64)
+    with pytest.raises(ValueError, match="pinned host"):
+        _check_tensor(t, "A_diag", (2, 3, 3), host_ok=True)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        _check_tensor(t, "X", (2, 3, 3))
+    with pytest.raises(ValueError):
+        _check_tensor(t.float(), "A_diag", (2, 3, 3), host_ok=True)
