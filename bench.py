@@ -133,6 +133,35 @@ def cpu_baseline(s, budget_s=10.0):
                       f"scaled by {N}/{Ns}"}
 
 
+def cpu_rates(budget_s=3.0):
+    """The oracle on the host cores for the other workloads, each on a bounded
+    sample (systems/s scaled to the whole workload)."""
+    import oracle
+    oracle.build()
+    out = {}
+    for name in ("kalman-N64-n8-d1", "kalman-N4096-n256-d16-rho0.99", "kalman-N2048-n32-d8-grad"):
+        s = inputs.workload(name)
+        N = s["A_diag"].shape[0]
+        Ns = min(N, 4)
+        while True:
+            t0 = time.perf_counter()
+            oracle.solve_system(s["A_diag"][:Ns], s["A_sub"][:Ns - 1], s["B"][:Ns])
+            t = time.perf_counter() - t0
+            if Ns >= N or t > budget_s / 4:
+                break
+            Ns = min(N, Ns * 4)
+        out[name] = {"value": (Ns / N) / t, "unit": "systems/s", "cores": 1, "kind": "oracle",
+                     "sample": f"block-Thomas factor+solve of the first {Ns} of {N} blocks ({t:.3f} s), "
+                               f"scaled by {N}/{Ns}"}
+    systems = inputs.mpc_batch(K=512, d=1, rho=0.95, seed=0)
+    t0 = time.perf_counter()
+    _, threads = oracle.factor_solve_batched(systems)
+    t = time.perf_counter() - t0
+    out["mpc-batch-512"] = {"value": 512 / t, "unit": "systems/s", "cores": threads, "kind": "oracle",
+                            "sample": f"all 512 systems, one system per thread ({t:.2f} s)"}
+    return out
+
+
 def _timed(fn, reps, stream, max_over_ranks):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -155,6 +184,18 @@ def other_workloads(dev, stream, world, max_over_ranks, args):
     from paper_2509_03015_gb300 import BatchSolver, Solver, block_tri_solve
     res = {}
     reps = max(2, args.steps // 5)
+    # -- the small case: one short system, latency of one call ------------------
+    name = "kalman-N64-n8-d1"
+    cfg = inputs.WORKLOADS[name]
+    s = inputs.workload(name)
+    Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
+    X = torch.empty_like(B)
+    sol = Solver(cfg["N"], cfg["n"], d_max=cfg["d"], stream=stream)
+    sol.factor_solve(Ad, As, B, X)
+    ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 20, stream, max_over_ranks)
+    res[name] = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms,
+                 "note": "one call = one persistent launch + status read-back"}
+    sol.close()
     # -- mixed precision at n = 256 --------------------------------------------
     name = "kalman-N4096-n256-d16-rho0.99"
     cfg = inputs.WORKLOADS[name]
@@ -445,6 +486,9 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s)
+        if "workloads" in out:
+            for name, r in cpu_rates().items():
+                out["workloads"].setdefault(name, {})["cpu_oracle"] = r
     solver.close()
     if rank == 0:
         print(json.dumps(out))
