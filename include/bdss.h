@@ -167,6 +167,12 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
 
+/* Launch configuration the handle chose at creation (host pointers, any may
+ * be NULL): resident CTAs per SM of its persistent kernel (from the
+ * occupancy calculator), the SM count, and the dynamic shared memory per CTA
+ * in bytes.  A full persistent grid has ctas_per_sm * sm_count CTAs. */
+bdss_status bdss_get_launch_config(bdss_handle h, int32_t *ctas_per_sm, int32_t *sm_count, int64_t *smem_bytes);
+
 /* Phase trace of the last launch that ran grid barriers (a persistent factor
  * or solve pass): release_ns[i] = %globaltimer (ns) when grid barrier i was
  * released; barrier 0 is the start-up barrier, then for each level l the

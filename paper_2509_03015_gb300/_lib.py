@@ -37,6 +37,7 @@ SIGNATURES = {
     "bdss_logdet": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "bdss_last_launch_stats": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bdss_last_trace": (_i32, [_vp, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32)]),
+    "bdss_get_launch_config": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "bdss_destroy": (_i32, [_vp]),
     "bdss_status_string": (ctypes.c_char_p, [_i32]),
     "bdss_last_cuda_error": (ctypes.c_char_p, []),

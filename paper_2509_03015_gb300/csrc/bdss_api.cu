@@ -24,6 +24,7 @@ struct bdss_ctx {
   Plan plan{};
   int sms = 0;
   int bps = 0;          // resident CTAs per SM of the persistent kernel
+  int bps_tc = 0;       // the same for the tiled path's tensor-core kernel (TF32 factor)
   size_t smem = 0;      // dynamic shared memory per CTA
   // workspace
   bool large = false;   // 64 < n <= 256: tiled path
@@ -139,7 +140,12 @@ template <typename T>
 static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, bool rhs) {
   const Plan &p = h->plan;
   const int esz = (int)sizeof(T);
-  if (h->persistent) {
+  // The TF32 factorisation runs sub-phase by sub-phase even in persistent
+  // mode: a kernel holding tcgen05 code gets one CTA per SM, so only the
+  // Schur-update tiles use that kernel and the Cholesky / substitution tasks
+  // keep the two-CTA FP32 kernel.
+  const bool tc_factor = sizeof(T) == 4 && h->tf32 && factor;
+  if (h->persistent && !tc_factor) {
     long long most = 1;
     for (int l = 0; l < p.L; ++l)
       for (int sub = 0; sub < 4; ++sub) {
@@ -275,12 +281,16 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
   if (h->large) {
     e = configure<double>(1, 1, &h->smem, &h->bps);  // raises every kernel's shared-memory limit
     if (e == cudaSuccess)
-      e = is_mixed(h) ? configure_large<float>(n, d_max, &h->smem, &h->bps)
-                      : configure_large<double>(n, d_max, &h->smem, &h->bps);
+      e = is_mixed(h) ? configure_large<float>(n, d_max, &h->smem, &h->bps, &h->bps_tc)
+                      : configure_large<double>(n, d_max, &h->smem, &h->bps, &h->bps_tc);
   } else {
     e = is_mixed(h) ? configure<float>(n, d_max, &h->smem, &h->bps) : configure<double>(n, d_max, &h->smem, &h->bps);
   }
-  if (e != cudaSuccess || h->bps < 1) { bdss_destroy(h); return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration); }
+  if (e == cudaSuccess && !h->large) h->bps_tc = h->bps;
+  if (e != cudaSuccess || h->bps < 1 || h->bps_tc < 1) {
+    bdss_destroy(h);
+    return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidConfiguration);
+  }
   const size_t nn = (size_t)n * n;
   const size_t slots = (size_t)(h->plan.off[h->plan.L] > 0 ? h->plan.off[h->plan.L] : 1);
   bool ok = cudaMalloc(&h->Ld, (size_t)N * nn * esz) == cudaSuccess;
@@ -587,6 +597,14 @@ bdss_status bdss_tc_selftest(double *max_rel_err) {
   cudaError_t e = run_tc_selftest(max_rel_err, &st);
   if (e != cudaSuccess) return cuda_fail(e);
   return (bdss_status)st;
+}
+
+bdss_status bdss_get_launch_config(bdss_handle h, int32_t *ctas_per_sm, int32_t *sm_count, int64_t *smem_bytes) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  if (ctas_per_sm) *ctas_per_sm = h->bps;
+  if (sm_count) *sm_count = h->sms;
+  if (smem_bytes) *smem_bytes = (int64_t)h->smem;
+  return BDSS_OK;
 }
 
 bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity, int32_t *count) {

@@ -577,23 +577,24 @@ __device__ void trsv_bwd_cta(const T *sL, int ld, int n, T *V, int nv) {
 }
 
 // Forward substitution L w = v for `nv` staged vectors (rows of V, stride
-// ld); L staged with reciprocal diagonal.  On this GPU one warp issues at
-// most one FP64 instruction per ~64 cycles and the SM's FP64 pipe needs
-// four or more warps to be full, so the work is spread over all warps: rows
-// are taken 8 at a time; the update of a row block from the rows already
-// solved runs over (vector, row) pairs on every thread, then one thread per
-// vector solves the 8 x 8 diagonal triangle.  Same FP64 operation count as
-// the row-by-row sweep.  All threads of the CTA must call it.
+// ldv), L an n x n lower-triangular tile (stride ldl, reciprocal diagonal),
+// both in shared memory.  On this GPU one warp issues at most one FP64
+// instruction per ~64 cycles and the SM's FP64 pipe needs four or more warps
+// to be full, so the work is spread over all warps: rows are taken 8 at a
+// time; the update of a row block from the rows already solved runs over
+// (vector, row) pairs on every thread, then one thread per vector solves the
+// 8 x 8 diagonal triangle.  Each vector receives the same operations in the
+// same order as the row-by-row sweep.  All threads call; ends with a barrier.
 template <typename T>
-__device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
+__device__ void trsv_tile_fwd(const T *sL, int ldl, int n, T *V, int ldv, int nv) {
   constexpr int RB = 8;
   for (int r0 = 0; r0 < n; r0 += RB) {
     const int rb = min(RB, n - r0);
     if (r0 > 0) {
       for (int t = threadIdx.x; t < nv * rb; t += blockDim.x) {
         const int i = t / nv, v = t - i * nv;
-        T *w = V + v * ld;
-        const T *lr = sL + (r0 + i) * ld;
+        T *w = V + (size_t)v * ldv;
+        const T *lr = sL + (size_t)(r0 + i) * ldl;
         T acc = w[r0 + i];
         for (int p = 0; p < r0; ++p) acc = fma(-lr[p], w[p], acc);
         w[r0 + i] = acc;
@@ -601,7 +602,7 @@ __device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
       __syncthreads();
     }
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      T *w = V + v * ld + r0;
+      T *w = V + (size_t)v * ldv + r0;
       T acc[RB];
 #pragma unroll
       for (int i = 0; i < RB; ++i) acc[i] = (i < rb) ? w[i] : T(0);
@@ -610,8 +611,8 @@ __device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
         if (i < rb) {
           T a = acc[i];
 #pragma unroll
-          for (int q = 0; q < i; ++q) a = fma(-sL[(r0 + i) * ld + r0 + q], acc[q], a);
-          acc[i] = a * sL[(r0 + i) * ld + r0 + i];
+          for (int q = 0; q < i; ++q) a = fma(-sL[(size_t)(r0 + i) * ldl + r0 + q], acc[q], a);
+          acc[i] = a * sL[(size_t)(r0 + i) * ldl + r0 + i];
         }
 #pragma unroll
       for (int i = 0; i < RB; ++i)
@@ -619,6 +620,52 @@ __device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
     }
     __syncthreads();
   }
+}
+
+// Backward substitution L^T z = t, same organisation from the last row block
+// up: the update of a row block from the rows below runs over (vector, row)
+// pairs, then one thread per vector solves the block's triangle.
+template <typename T>
+__device__ void trsv_tile_bwd(const T *sL, int ldl, int n, T *V, int ldv, int nv) {
+  constexpr int RB = 8;
+  for (int r1 = n; r1 > 0; r1 -= RB) {
+    const int r0 = max(0, r1 - RB), rb = r1 - r0;
+    if (r1 < n) {
+      for (int t = threadIdx.x; t < nv * rb; t += blockDim.x) {
+        const int i = t / nv, v = t - i * nv;
+        T *w = V + (size_t)v * ldv;
+        T acc = w[r0 + i];
+        for (int p = r1; p < n; ++p) acc = fma(-sL[(size_t)p * ldl + r0 + i], w[p], acc);
+        w[r0 + i] = acc;
+      }
+      __syncthreads();
+    }
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      T *w = V + (size_t)v * ldv + r0;
+      T acc[RB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) acc[i] = (i < rb) ? w[i] : T(0);
+#pragma unroll
+      for (int i = RB - 1; i >= 0; --i)
+        if (i < rb) {
+          T a = acc[i];
+#pragma unroll
+          for (int q = i + 1; q < RB; ++q)
+            if (q < rb) a = fma(-sL[(size_t)(r0 + q) * ldl + r0 + i], acc[q], a);
+          acc[i] = a * sL[(size_t)(r0 + i) * ldl + r0 + i];
+        }
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        if (i < rb) w[i] = acc[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Square tiles with one stride for L and the vectors.
+template <typename T>
+__device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
+  trsv_tile_fwd(sL, ld, n, V, ld, nv);
 }
 
 // Backward substitution L^T z = t for `nv` staged vectors.

@@ -11,7 +11,7 @@ namespace bdss {
 
 enum { kSubA1 = 0, kSubA2 = 1, kSubB = 2, kSubC = 3 };
 
-template <typename T>
+template <typename T, bool kTc>
 __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem, int *s_flag, TcState *tc,
                           int rank) {
   const int n = a.p.n, d = a.d;
@@ -29,7 +29,7 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
       if (v * VT < largeA2_vectors(a, l, j, factor)) largeA2(a, l, j, v, factor, smem);
     }
   } else if (sub == kSubB) {
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (kTc) {
       if (tc && factor) {
         // D and E tiles on the tensor cores, RHS tiles on CUDA cores
         const int nTC = largeB_tc_tiles(n), nR = largeB_tiles(n, false, d), nTB = nTC + nR;
@@ -53,7 +53,7 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
   return true;
 }
 
-template <typename T>
+template <typename T, bool kTc>
 __device__ void large_body(const Args<T> &a, int factor, int rhs, unsigned char *smem_raw, int *s_flag,
                            TcState *tc) {
   T *smem = reinterpret_cast<T *>(smem_raw);
@@ -62,53 +62,68 @@ __device__ void large_body(const Args<T> &a, int factor, int rhs, unsigned char 
   if (rank < 0) return;
   for (int l = 0; l < a.p.L; ++l) {
     if (factor) {
-      large_sub(a, l, kSubA1, true, smem, s_flag, tc, rank);
+      large_sub<T, kTc>(a, l, kSubA1, true, smem, s_flag, tc, rank);
       if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
     }
-    large_sub(a, l, kSubA2, factor != 0, smem, s_flag, tc, rank);
+    large_sub<T, kTc>(a, l, kSubA2, factor != 0, smem, s_flag, tc, rank);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
-    large_sub(a, l, kSubB, factor != 0, smem, s_flag, tc, rank);
+    large_sub<T, kTc>(a, l, kSubB, factor != 0, smem, s_flag, tc, rank);
     if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
   if (rank == 0) largeTop(a, factor != 0, reinterpret_cast<double *>(smem_raw), s_flag);
   if (!rhs || a.p.L == 0) return;
   if (!grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   for (int l = a.p.L - 1; l >= 0; --l) {
-    large_sub(a, l, kSubC, false, smem, s_flag, tc, rank);
+    large_sub<T, kTc>(a, l, kSubC, false, smem, s_flag, tc, rank);
     if (l > 0 && !grid_barrier(a.st, a.timeout_ns, ++bar, a.skip_barrier)) return;
   }
 }
 
 // The tensor-core state (TMEM, mbarriers) is set up once per CTA when the
-// TF32 mode is on and released on every way out of the kernel body.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_large_persistent(const __grid_constant__ Args<T> a, int factor,
-                                                               int rhs) {
+// TF32 mode factors and released on every way out of the kernel body.  The
+// tensor-core variant (kTc) is a separate kernel: the occupancy calculator
+// allows one CTA per SM for a kernel that contains tcgen05 code, while the
+// FP32 tiles without it fit two.
+// Register cap: FP32 tiles fit two CTAs per SM in shared memory, so the
+// registers must allow two as well; FP64 is shared-memory limited to one.
+#define BDSS_LARGE_MAXNREG(T) __maxnreg__(sizeof(T) == 4 ? 120 : 255)
+
+template <typename T, bool kTc>
+__global__ void __launch_bounds__(kThreads) BDSS_LARGE_MAXNREG(T)
+    k_large_persistent(const __grid_constant__ Args<T> a, int factor, int rhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_flag;
-  __shared__ uint64_t s_bars[2];
-  __shared__ uint32_t s_tmem;
-  TcState tc;
-  const bool use_tc = std::is_same<T, float>::value && a.tf32 && factor;
-  if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
-  large_body(a, factor, rhs, smem_raw, &s_flag, use_tc ? &tc : nullptr);
-  if (use_tc) tc_end(tc);
+  if constexpr (kTc) {
+    __shared__ uint64_t s_bars[2];
+    __shared__ uint32_t s_tmem;
+    TcState tc;
+    const bool use_tc = a.tf32 && factor;
+    if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
+    large_body<T, true>(a, factor, rhs, smem_raw, &s_flag, use_tc ? &tc : nullptr);
+    if (use_tc) tc_end(tc);
+  } else {
+    large_body<T, false>(a, factor, rhs, smem_raw, &s_flag, nullptr);
+  }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_large_sub(const __grid_constant__ Args<T> a, int l, int sub,
-                                                        int factor) {
+template <typename T, bool kTc>
+__global__ void __launch_bounds__(kThreads) BDSS_LARGE_MAXNREG(T)
+    k_large_sub(const __grid_constant__ Args<T> a, int l, int sub, int factor) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_flag;
-  __shared__ uint64_t s_bars[2];
-  __shared__ uint32_t s_tmem;
   if (ld_relaxed_i32(&a.st->status) != 0) return;
-  TcState tc;
-  const bool use_tc = std::is_same<T, float>::value && a.tf32 && factor && sub == kSubB;
-  if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
-  large_sub(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, use_tc ? &tc : nullptr,
-            (int)blockIdx.x);
-  if (use_tc) tc_end(tc);
+  if constexpr (kTc) {
+    __shared__ uint64_t s_bars[2];
+    __shared__ uint32_t s_tmem;
+    TcState tc;
+    const bool use_tc = a.tf32 && factor && sub == kSubB;
+    if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
+    large_sub<T, true>(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, use_tc ? &tc : nullptr,
+                       (int)blockIdx.x);
+    if (use_tc) tc_end(tc);
+  } else {
+    large_sub<T, false>(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, nullptr, (int)blockIdx.x);
+  }
 }
 
 template <typename T>
@@ -212,11 +227,12 @@ size_t smem_bytes_large(int n, int d) {
 }
 
 template <typename T>
-cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm) {
+cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm, int *blocks_per_sm_tc) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const void *kernels[] = {(const void *)k_large_persistent<T>, (const void *)k_large_sub<T>,
+  const void *kernels[] = {(const void *)k_large_persistent<T, false>, (const void *)k_large_sub<T, false>,
+                           (const void *)k_large_persistent<float, true>, (const void *)k_large_sub<float, true>,
                            (const void *)k_large_top<T>, (const void *)k_residual_rows,
                            (const void *)k_tc_selftest};
   for (const void *k : kernels) {
@@ -226,12 +242,22 @@ cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   }
   const size_t sm = smem_bytes_large<T>(n, d);
-  int occ = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_large_persistent<T>, kThreads, sm);
+  int occ = 0, occ_tc = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_large_persistent<T, false>, kThreads, sm);
+  if (e == cudaSuccess && sizeof(T) == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tc, k_large_persistent<float, true>, kThreads, sm);
   if (e != cudaSuccess) return e;
   *smem = sm;
   *blocks_per_sm = occ;
+  *blocks_per_sm_tc = sizeof(T) == 4 ? occ_tc : occ;
   return cudaSuccess;
+}
+
+// The tensor-core kernel runs only when the TF32 mode factors.
+template <typename T>
+bool large_uses_tc(const Args<T> &a, int factor) {
+  return sizeof(T) == 4 && a.tf32 && factor;
 }
 
 template <typename T>
@@ -240,13 +266,21 @@ cudaError_t launch_large_persistent(const Args<T> &a, int factor, int rhs, int g
   if (!rhs) copy.d = 0;
   int f = factor, r = rhs;
   void *params[] = {(void *)&copy, (void *)&f, (void *)&r};
-  return cudaLaunchCooperativeKernel((const void *)k_large_persistent<T>, dim3(grid), dim3(kThreads), params, smem,
-                                     s);
+  const void *k = (const void *)k_large_persistent<T, false>;
+  if constexpr (sizeof(T) == 4)
+    if (large_uses_tc(a, factor)) k = (const void *)k_large_persistent<float, true>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), params, smem, s);
 }
 
 template <typename T>
 cudaError_t launch_large_sub(const Args<T> &a, int l, int sub, int factor, int grid, size_t smem, cudaStream_t s) {
-  k_large_sub<T><<<grid, kThreads, smem, s>>>(a, l, sub, factor);
+  if constexpr (sizeof(T) == 4) {
+    if (large_uses_tc(a, factor) && sub == kSubB) {
+      k_large_sub<float, true><<<grid, kThreads, smem, s>>>(a, l, sub, factor);
+      return cudaGetLastError();
+    }
+  }
+  k_large_sub<T, false><<<grid, kThreads, smem, s>>>(a, l, sub, factor);
   return cudaGetLastError();
 }
 
@@ -385,7 +419,7 @@ cudaError_t launch_residual_rows(long long N, int n, int d, const double *A_diag
 
 #define BDSS_INSTANTIATE_LARGE(T)                                                                        \
   template size_t smem_bytes_large<T>(int, int);                                                         \
-  template cudaError_t configure_large<T>(int, int, size_t *, int *);                                    \
+  template cudaError_t configure_large<T>(int, int, size_t *, int *, int *);                             \
   template cudaError_t launch_large_persistent<T>(const Args<T> &, int, int, int, size_t, cudaStream_t); \
   template cudaError_t launch_large_sub<T>(const Args<T> &, int, int, int, int, size_t, cudaStream_t);   \
   template cudaError_t launch_large_top<T>(const Args<T> &, int, size_t, cudaStream_t);

@@ -25,7 +25,8 @@ constexpr int kKc = 32;     // k-chunk staged per gemm step
 constexpr int kTilePad = kTile + 1;
 
 __host__ __device__ inline int ntiles(int n) { return (n + kTile - 1) / kTile; }
-__host__ __device__ inline int vec_tile(int elem_size) { return elem_size == 8 ? 32 : 64; }
+// Vectors per forward-substitution task: one 64-wide gemm tile of them.
+__host__ __device__ inline int vec_tile(int elem_size) { return 64; }
 
 // Strided matrix view: element (r, c) at p[r * rs + c * cs]; zero outside
 // rows x cols.  Global views load through L2 (written by other CTAs across
@@ -122,7 +123,7 @@ __device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_
       sT[r * ld + c] = v;
     }
     __syncthreads();
-    const int bad = chol_staged(sT, ld, kb, s_flag);
+    const int bad = blockDim.x >= 64 ? chol_fused(sT, ld, kb, sT, 0, sT, 0, s_flag) : chol_staged(sT, ld, kb, s_flag);
     if (bad) return k0 + bad;
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
       const int r = e / kb, c = e - r * kb;
@@ -141,16 +142,7 @@ __device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_
         sP[r * ld + c] = v;
       }
       __syncthreads();
-      for (int r = threadIdx.x; r < ib; r += blockDim.x) {
-        T *w = sP + r * ld;
-        for (int q = 0; q < kb; ++q) {
-          T acc = w[q];
-          const T *lq = sT + q * ld;
-          for (int p = 0; p < q; ++p) acc = fma(-lq[p], w[p], acc);
-          w[q] = acc * lq[q];
-        }
-      }
-      __syncthreads();
+      trsv_tile_fwd(sT, ld, kb, sP, ld, ib);  // each panel row x solves L_kk x = s
       for (int e = threadIdx.x; e < ib * kb; e += blockDim.x) {
         const int r = e / kb, c = e - r * kb;
         M[(long long)(i0 + r) * n + k0 + c] = sP[r * ld + c];
@@ -215,16 +207,7 @@ __device__ void trsv_fwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
       sT[r * kTilePad + c] = (r < rb && c <= r) ? ldcg(L + (long long)(r0 + r) * n + r0 + c) : T(0);
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      T *w = sV + (long long)v * lv + r0;
-      for (int r = 0; r < rb; ++r) {
-        T acc = w[r];
-        const T *lr = sT + r * kTilePad;
-        for (int p = 0; p < r; ++p) acc = fma(-lr[p], w[p], acc);
-        w[r] = acc * lr[r];
-      }
-    }
-    __syncthreads();
+    trsv_tile_fwd(sT, kTilePad, rb, sV + r0, lv, nv);
   }
 }
 
@@ -261,15 +244,7 @@ __device__ void trsv_bwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
       sT[r * kTilePad + c] = (r < rb && c <= r) ? ldcg(L + (long long)(r0 + r) * n + r0 + c) : T(0);
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-      T *w = sV + (long long)v * lv + r0;
-      for (int r = rb - 1; r >= 0; --r) {
-        T acc = w[r];
-        for (int p = r + 1; p < rb; ++p) acc = fma(-sT[p * kTilePad + r], w[p], acc);
-        w[r] = acc * sT[r * kTilePad + r];
-      }
-    }
-    __syncthreads();
+    trsv_tile_bwd(sT, kTilePad, rb, sV + r0, lv, nv);
   }
 }
 

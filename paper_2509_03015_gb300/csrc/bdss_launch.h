@@ -28,7 +28,8 @@ cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, c
 // large-block path (64 < n <= 256)
 constexpr int kMaxNLarge = 256;
 template <typename T> size_t smem_bytes_large(int n, int d);
-template <typename T> cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm);
+template <typename T>
+cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm, int *blocks_per_sm_tc);
 template <typename T>
 cudaError_t launch_large_persistent(const Args<T> &a, int factor, int rhs, int grid, size_t smem, cudaStream_t s);
 template <typename T>

@@ -118,6 +118,14 @@ class Solver:
         _lib.check(self.lib.bdss_last_launch_stats(self.h, ctypes.byref(k), ctypes.byref(b)), "bdss_last_launch_stats")
         return k.value, b.value
 
+    def launch_config(self):
+        """(resident CTAs per SM, SM count, dynamic shared memory bytes per
+        CTA) of this handle's persistent kernel."""
+        c, m, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _lib.check(self.lib.bdss_get_launch_config(self.h, ctypes.byref(c), ctypes.byref(m), ctypes.byref(b)),
+                   "bdss_get_launch_config")
+        return c.value, m.value, b.value
+
     @property
     def plan_levels(self):
         """Levels L with eliminations (N_{l+1} = ceil(N_l / 2) down to 1)."""

@@ -20,6 +20,7 @@ def test_trace_argument_checks(lib):
     cnt = ctypes.c_int32()
     buf = (ctypes.c_int64 * 4)()
     assert lib.bdss_last_trace(None, buf, 4, ctypes.byref(cnt)) == 1
+    assert lib.bdss_get_launch_config(None, None, None, None) == 1
 
 
 def _bench():

@@ -35,3 +35,21 @@ def test_trace_stamps_every_barrier(precision):
         assert stamps[-1] - stamps[0] < 10_000_000_000
     finally:
         sol.close()
+
+
+@pytest.mark.parametrize("n,precision", [(64, "fp64"), (64, "fp32_ir"), (256, "fp64"), (256, "fp32_ir"),
+                                         (256, "tf32_ir")])
+def test_launch_config_is_resident(n, precision):
+    # the persistent grid must fit on the GPU at once (cooperative launch):
+    # at least one CTA per SM, with the shared memory the occupancy
+    # calculator was given
+    from paper_2509_03015_gb300 import Solver
+    sol = Solver(64, n, d_max=16 if n == 256 else 4, precision=precision)
+    try:
+        per_sm, sms, smem = sol.launch_config()
+        props = torch.cuda.get_device_properties(0)
+        assert sms == props.multi_processor_count
+        assert 1 <= per_sm <= 8 and 0 < smem <= 232448
+        print(f"n={n} {precision}: {per_sm} CTAs/SM, {smem} B shared memory")
+    finally:
+        sol.close()
