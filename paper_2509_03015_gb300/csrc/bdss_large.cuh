@@ -75,6 +75,34 @@ __device__ void gemm_nt_tile(T (&acc)[4][4], const VA &A, int r0, const VB &B, i
   }
 }
 
+// The same product for a narrow output: rows r0..r0+63 by up to 16 columns
+// from c0 (right-hand sides).  Thread t owns row t / 4 and columns
+// 4 (t % 4) + j, so every thread works when d <= 16 (the square tile would
+// leave three quarters of its FMAs on zero columns).  sB needs kKc x 17.
+constexpr int kNarrow = 16;
+template <typename T, typename VA, typename VB>
+__device__ void gemm_nt_narrow(T (&acc)[4], const VA &A, int r0, const VB &B, int c0, int K, T *sA, T *sB) {
+  const int tr = threadIdx.x >> 2, tc = threadIdx.x & 3;
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+    for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
+      const int m = e / kKc, k = e - m * kKc;
+      sA[k * kTilePad + m] = (k0 + k) < K ? (T)A.at(r0 + m, k0 + k) : T(0);
+    }
+    for (int e = threadIdx.x; e < kNarrow * kKc; e += blockDim.x) {
+      const int m = e / kKc, k = e - m * kKc;
+      sB[k * (kNarrow + 1) + m] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
+    }
+    __syncthreads();
+    const int kc = min(kKc, K - k0);
+    for (int k = 0; k < kc; ++k) {
+      const T a = sA[k * kTilePad + tr];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fma(a, sB[k * (kNarrow + 1) + 4 * tc + j], acc[j]);
+    }
+    __syncthreads();
+  }
+}
+
 // Shared memory (in elements of FP64) of the FP64 top block: d solution
 // vectors plus the tile work area (it never stages coupling vectors).
 __host__ __device__ inline size_t smem_large_top(int n, int d) {
@@ -382,27 +410,26 @@ __device__ void largeB(const Args<T> &a, int l, long long k, int t, bool factor,
   } else {
     const int ti = t - nD - nE;
     const size_t boff = (size_t)orig * n * d;
-    for (int c0 = 0; c0 < d; c0 += kTile) {
-      T acc[4][4] = {};
+    for (int c0 = 0; c0 < d; c0 += kNarrow) {
+      T acc[4] = {};
       // y as the "B" operand: (c, q) -> y[q][c]
       const View<T> Ym{a.Y + (size_t)((s - 1) << l) * n * d + c0, 1, d, d - c0, n};
       const View<T> Yp{a.Y + (size_t)((s + 1) << l) * n * d + c0, 1, d, d - c0, n};
-      if (hasM) gemm_nt_tile(acc, W0, ti * kTile, Ym, 0, n, sA, sB);
-      if (hasP) gemm_nt_tile(acc, W1, ti * kTile, Yp, 0, n, sA, sB);
+      if (hasM) gemm_nt_narrow(acc, W0, ti * kTile, Ym, 0, n, sA, sB);
+      if (hasP) gemm_nt_narrow(acc, W1, ti * kTile, Yp, 0, n, sA, sB);
+      const int r = ti * kTile + (threadIdx.x >> 2);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int r = ti * kTile + 4 * tm + i, c = c0 + 4 * tn + jj;
-          if (r < n && c < d) {
-            const size_t o = boff + (size_t)r * d + c;
-            T base;
-            if (l == 0 && a.B64) base = (T)ldcg(a.B64 + o);
-            else if (l == 0 && a.Bt) base = ldcg(a.Bt + o);
-            else base = ldcg(a.Y + o);
-            a.Y[o] = base - acc[i][jj];
-          }
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = c0 + 4 * (threadIdx.x & 3) + jj;
+        if (r < n && c < d) {
+          const size_t o = boff + (size_t)r * d + c;
+          T base;
+          if (l == 0 && a.B64) base = (T)ldcg(a.B64 + o);
+          else if (l == 0 && a.Bt) base = ldcg(a.Bt + o);
+          else base = ldcg(a.Y + o);
+          a.Y[o] = base - acc[jj];
         }
+      }
       __syncthreads();
     }
   }
@@ -502,21 +529,19 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
   const View<T> WRq{W + (size_t)j * nn, 1, n, n, n};
   const View<T> Xm{a.Y + (size_t)((j - 1) << l) * nd, 1, d, d, n};
   const View<T> Xp{a.Y + (size_t)((j + 1) << l) * nd, 1, d, d, n};
-  const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
   for (int R = 0; R < ntiles(n); ++R)
-    for (int c0 = 0; c0 < d; c0 += kTile) {
-      T acc[4][4] = {};
+    for (int c0 = 0; c0 < d; c0 += kNarrow) {
+      T acc[4] = {};
       const View<T> Xmc{Xm.p + c0, 1, d, d - c0, n};
       const View<T> Xpc{Xp.p + c0, 1, d, d - c0, n};
-      gemm_nt_tile(acc, WLq, R * kTile, Xmc, 0, n, sA, sB);
-      if (hasR) gemm_nt_tile(acc, WRq, R * kTile, Xpc, 0, n, sA, sB);
+      gemm_nt_narrow(acc, WLq, R * kTile, Xmc, 0, n, sA, sB);
+      if (hasR) gemm_nt_narrow(acc, WRq, R * kTile, Xpc, 0, n, sA, sB);
+      const int q = R * kTile + (threadIdx.x >> 2);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int q = R * kTile + 4 * tm + i, c = c0 + 4 * tn + jj;
-          if (q < n && c < d) sV[(size_t)c * lv + q] = ldcg(Yj + (size_t)q * d + c) - acc[i][jj];
-        }
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = c0 + 4 * (threadIdx.x & 3) + jj;
+        if (q < n && c < d) sV[(size_t)c * lv + q] = ldcg(Yj + (size_t)q * d + c) - acc[jj];
+      }
       __syncthreads();
     }
   trsv_bwd_blocked(a.Ld + (size_t)orig * nn, n, sV, d, work);
