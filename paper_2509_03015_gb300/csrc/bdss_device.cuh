@@ -726,11 +726,15 @@ __host__ __device__ inline int split_parts(long long items, int capacity, int ma
 constexpr int kMaxPartsA = 8;  // coupling columns of phase A over CTAs
 constexpr int kMaxPartsB = 8;  // output entries of the FP64 phase B over CTAs
 
+// Blocks below n = 32 hold too little work per column to be worth a CTA
+// each: no split there (fewer CTAs also make the grid barriers cheaper).
+constexpr int kSplitMinN = 32;
 template <typename T> __host__ __device__ inline int parts_A(const Plan &p, int l, bool factor, int capacity) {
-  return factor ? split_parts(p.Nl[l] / 2, capacity, kMaxPartsA) : 1;
+  return (factor && p.n >= kSplitMinN) ? split_parts(p.Nl[l] / 2, capacity, kMaxPartsA) : 1;
 }
 template <typename T> __host__ __device__ inline int parts_B(const Plan &p, int l, bool factor, int capacity) {
-  return (factor && sizeof(T) == 8) ? split_parts((p.Nl[l] + 1) / 2, capacity, kMaxPartsB) : 1;
+  return (factor && sizeof(T) == 8 && p.n >= kSplitMinN) ? split_parts((p.Nl[l] + 1) / 2, capacity, kMaxPartsB)
+                                                          : 1;
 }
 
 // s[(c - c0)*ld + i] = g[i][c] for c0 <= c < c1 (columns of an n x n block).

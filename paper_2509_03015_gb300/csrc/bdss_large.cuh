@@ -50,28 +50,69 @@ struct View {
 template <typename T, typename VA, typename VB>
 __device__ void gemm_nt_tile(T (&acc)[4][4], const VA &A, int r0, const VB &B, int c0, int K, T *sA, T *sB) {
   const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
-  for (int k0 = 0; k0 < K; k0 += kKc) {
-    for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
-      const int m = e / kKc, k = e - m * kKc;
-      const bool kin = (k0 + k) < K;
-      sA[k * kTilePad + m] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
-      sB[k * kTilePad + m] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
-    }
-    __syncthreads();
-    const int kc = min(kKc, K - k0);
-    for (int k = 0; k < kc; ++k) {
-      T a[4], b[4];
+  if constexpr (sizeof(T) == 8) {
+    // FP64 (one CTA per SM): the next k-chunk is loaded into registers while
+    // the current one is multiplied, so its global latency overlaps the DFMAs
+    constexpr int kPer = kTile * kKc / kThreads;  // elements per thread and operand
+    T ra[kPer], rb[kPer];
+    auto load = [&](int k0) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = sA[k * kTilePad + 4 * tm + i];
-        b[i] = sB[k * kTilePad + 4 * tn + i];
+      for (int q = 0; q < kPer; ++q) {
+        const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+        const bool kin = (k0 + k) < K;
+        ra[q] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
+        rb[q] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
       }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += kKc) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int q = 0; q < kPer; ++q) {
+        const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+        sA[k * kTilePad + m] = ra[q];
+        sB[k * kTilePad + m] = rb[q];
+      }
+      __syncthreads();
+      if (k0 + kKc < K) load(k0 + kKc);
+      const int kc = min(kKc, K - k0);
+      for (int k = 0; k < kc; ++k) {
+        T a[4], b[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int i = 0; i < 4; ++i) {
+          a[i] = sA[k * kTilePad + 4 * tm + i];
+          b[i] = sB[k * kTilePad + 4 * tn + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
+  } else {
+    for (int k0 = 0; k0 < K; k0 += kKc) {
+      for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
+        const int m = e / kKc, k = e - m * kKc;
+        const bool kin = (k0 + k) < K;
+        sA[k * kTilePad + m] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
+        sB[k * kTilePad + m] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
+      }
+      __syncthreads();
+      const int kc = min(kKc, K - k0);
+      for (int k = 0; k < kc; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a[i] = sA[k * kTilePad + 4 * tm + i];
+          b[i] = sB[k * kTilePad + 4 * tn + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
   }
 }
 
