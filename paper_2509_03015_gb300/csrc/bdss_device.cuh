@@ -668,20 +668,6 @@ __device__ void trsv_fwd_rows(const T *sL, int ld, int n, T *V, int nv) {
   trsv_tile_fwd(sL, ld, n, V, ld, nv);
 }
 
-// Backward substitution L^T z = t for `nv` staged vectors.
-template <typename T>
-__device__ void trsv_bwd_rows(const T *sL, int ld, int n, T *V, int nv) {
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    T *w = V + v * ld;
-    for (int r = n - 1; r >= 0; --r) {
-      T acc = w[r];
-      for (int p = r + 1; p < n; ++p) acc = fma(-sL[p * ld + r], w[p], acc);
-      w[r] = acc * sL[r * ld + r];
-    }
-  }
-}
-
-
 // Shared-memory words (in T) of each phase.
 // Phase A holds L, one pass of n coupling vectors and the d RHS vectors;
 // phase B holds two W^T blocks and two d-vector sets.  (Two passes / two
