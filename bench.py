@@ -266,6 +266,7 @@ def run_reference(args, world, rank):
         return
     import oracle
     oracle.build()
+    cfg = inputs.WORKLOADS[WORKLOAD]
     s = inputs.workload(WORKLOAD)
     N = s["A_diag"].shape[0]
     Ns = 1024
@@ -284,7 +285,9 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps * (N / Ns),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "n": 64, "d": 4, "path": "CPU FP64 block-Thomas oracle"},
+        "config": {"workload": WORKLOAD, "N": N, "n": cfg["n"], "d": cfg["d"], "m": cfg["m"], "rho": cfg["rho"],
+                   "seed": cfg["seed"], "path": "CPU FP64 block-Thomas oracle on the host cores",
+                   "l2": "n/a (host)", "parallelism": "1 core"},
         "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
