@@ -78,7 +78,8 @@ def test_fp64_separate_factor_then_solve(oracle_mod, N, n, d):
     assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
 
 
-@pytest.mark.parametrize("N,n,d", [(3, 4, 1), (64, 8, 1), (1000, 16, 2), (4099, 12, 1)])
+@pytest.mark.parametrize("N,n,d", [(3, 4, 1), (64, 8, 1), (1000, 16, 2), (4099, 12, 1),
+                                   (1, 5, 3), (2, 16, 8), (100, 3, 5), (255, 16, 8), (256, 1, 1)])
 def test_per_level_launches_match_persistent(N, n, d):
     """The per-level launch structure (Algorithms 4, 7) and the persistent
     kernel run the same arithmetic in the same order: bitwise equal."""
@@ -273,5 +274,25 @@ def test_reported_backward_error_matches_oracle(oracle_mod, N, n, d):
         ref = oracle_mod.backward_error(s["A_diag"], s["A_sub"], X.cpu().numpy(), s["B"])
         assert 1e-12 < ref < 1e-3
         assert abs(reported - ref) <= 1e-5 * ref
+    finally:
+        solver.close()
+
+
+@pytest.mark.parametrize("N,n,blk", [(64, 8, 0), (64, 8, 12), (200, 16, 96), (7, 4, 6)])
+def test_small_systems_report_not_spd(N, n, blk):
+    # a failing pivot in a small system (few CTAs, tail levels only)
+    from paper_2509_03015_gb300 import BDSSError, Solver
+    s = inputs.random_btd(N, n, 1, seed=4)
+    s["A_diag"][blk] -= 1000.0 * np.eye(n)
+    Ad, As, B = _dev(s)
+    solver = Solver(N, n, d_max=1)
+    try:
+        with pytest.raises(BDSSError) as e:
+            solver.factor_solve(Ad, As, B)
+        assert e.value.status == 2
+        if blk == 0:
+            assert e.value.info.block == 0
+        else:
+            assert e.value.info.level == (blk & -blk).bit_length() - 1 and e.value.info.block == blk
     finally:
         solver.close()
