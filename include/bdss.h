@@ -220,8 +220,11 @@ bdss_status bdss_batch_set_inputs(bdss_batch b, const double *const *A_diag_k, c
 bdss_status bdss_batch_launch(bdss_batch b, int32_t use_graph);
 /* Wait for the last launch; info_k[k] (K entries, may be NULL) gets the
  * instance's pivot failure (level/block) with its status code in `reserved`;
- * latency_us_k[k] (may be NULL) the time from the instance's first task start
- * to its last task end inside the launch.  Returns the first non-OK status. */
+ * latency_us_k[k] (may be NULL) the time from the launch's first task start
+ * to the instance's last task end, i.e. how long after the batch began the
+ * instance's solution was complete.  Instances are queued in groups of
+ * ascending work, each group stage by stage, so small instances complete
+ * early.  Returns the first non-OK status. */
 bdss_status bdss_batch_wait(bdss_batch b, bdss_info *info_k, double *latency_us_k);
 /* Time every candidate (threads per CTA in {32,64,128,256} >= max n_k;
  * items per task in {1,2,4}) on the bound inputs, keep the fastest for this

@@ -174,39 +174,78 @@ struct bdss_batch_ctx {
   unsigned long long *h_t = nullptr;   // pinned, 2K
 };
 
+// Queue order.  The instances with the most work (N n^3, the top
+// 1/kBatchGroups) form one stage-major sequence; the others form a second
+// sequence of groups of ascending work, each group stage-major (within a
+// stage, larger instances first).  The two sequences are merged in
+// proportion to their work, so the large instances advance through the
+// whole launch (their thin last stages end together with the rest), while
+// the small ones complete early instead of all instances finishing together
+// at the end of a fully stage-major queue.  Tasks never wait on a later
+// position of the queue, so every wait ends.
+constexpr int kBatchGroups = 8;
+
 static bdss_status batch_build_tasks(bdss_batch_ctx *b) {
-  // stage-major order; within a stage, larger instances first
   std::vector<int> order(b->K);
   for (int k = 0; k < b->K; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return b->N[x] * b->n[x] * b->n[x] > b->N[y] * b->n[y] * b->n[y];
-  });
-  std::vector<Task> tasks;
+  auto work = [&](int k) { return (double)b->N[k] * b->n[k] * b->n[k] * b->n[k]; };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) < work(y); });
   std::vector<int> nst(b->K), off(b->K);
-  int maxst = 0, acc = 0;
+  int acc = 0;
   for (int k = 0; k < b->K; ++k) {
     nst[k] = 3 * b->host_args[k].p.L + 1;
     off[k] = acc;
     acc += nst[k];
-    maxst = std::max(maxst, nst[k]);
   }
   b->total_stages = acc;
-  for (int s = 0; s < maxst; ++s)
-    for (int k : order) {
-      if (s >= nst[k]) continue;
-      const int L = b->host_args[k].p.L;
-      const long long items = stage_items(b->N[k], L, s);
-      const int need = s > 0 ? (int)stage_items(b->N[k], L, s - 1) : 0;
-      for (long long f = 0; f < items; f += b->items) {
-        Task t;
-        t.inst = k;
-        t.stage = s;
-        t.first = f;
-        t.count = (int)std::min<long long>(b->items, items - f);
-        t.need = need;
-        tasks.push_back(t);
+  // stage-major tasks of a group, with their work (items x n^3)
+  auto emit = [&](std::vector<int> grp, std::vector<Task> &out, std::vector<double> &w) {
+    std::stable_sort(grp.begin(), grp.end(), [&](int x, int y) { return work(x) > work(y); });
+    int maxst = 0;
+    for (int k : grp) maxst = std::max(maxst, nst[k]);
+    for (int s = 0; s < maxst; ++s)
+      for (int k : grp) {
+        if (s >= nst[k]) continue;
+        const int L = b->host_args[k].p.L;
+        const long long items = stage_items(b->N[k], L, s);
+        const int need = s > 0 ? (int)stage_items(b->N[k], L, s - 1) : 0;
+        for (long long f = 0; f < items; f += b->items) {
+          Task t;
+          t.inst = k;
+          t.stage = s;
+          t.first = f;
+          t.count = (int)std::min<long long>(b->items, items - f);
+          t.need = need;
+          out.push_back(t);
+          w.push_back((double)t.count * b->n[k] * b->n[k] * b->n[k]);
+        }
       }
+  };
+  const int G = std::min(kBatchGroups, b->K);
+  const size_t cut = (size_t)b->K * (G - 1) / G;  // instances [cut, K) form the large sequence
+  std::vector<Task> big, small;
+  std::vector<double> wbig, wsmall;
+  emit(std::vector<int>(order.begin() + cut, order.end()), big, wbig);
+  for (int g = 0; g < G - 1; ++g)
+    emit(std::vector<int>(order.begin() + (size_t)b->K * g / G, order.begin() + (size_t)b->K * (g + 1) / G), small,
+         wsmall);
+  double tb = 0, ts = 0;
+  for (double x : wbig) tb += x;
+  for (double x : wsmall) ts += x;
+  std::vector<Task> tasks;
+  tasks.reserve(big.size() + small.size());
+  size_t ib = 0, is = 0;
+  double cb = 0, cs = 0;
+  while (ib < big.size() || is < small.size()) {
+    const bool take_big = is >= small.size() || (ib < big.size() && cb / (tb > 0 ? tb : 1) <= cs / (ts > 0 ? ts : 1));
+    if (take_big) {
+      cb += wbig[ib];
+      tasks.push_back(big[ib++]);
+    } else {
+      cs += wsmall[is];
+      tasks.push_back(small[is++]);
     }
+  }
   b->ntasks = (long long)tasks.size();
   cudaFree(b->d_tasks);
   b->d_tasks = nullptr;
@@ -432,6 +471,8 @@ bdss_status bdss_batch_wait(bdss_batch b, bdss_info *info_k, double *latency_us_
                         b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return BDSS_ERR_CUDA;
+  unsigned long long t_start = ~0ull;  // first task start of the launch
+  for (int k = 0; k < b->K; ++k) t_start = std::min(t_start, b->h_t[k]);
   bdss_status worst = BDSS_OK;
   for (int k = 0; k < b->K; ++k) {
     const int st = b->h_status[k].status;
@@ -443,8 +484,8 @@ bdss_status bdss_batch_wait(bdss_batch b, bdss_info *info_k, double *latency_us_
       info_k[k].backward_err = -1.0;
     }
     if (latency_us_k) {
-      const unsigned long long t0 = b->h_t[k], t1 = b->h_t[b->K + k];
-      latency_us_k[k] = (t1 >= t0 && t0 != ~0ull) ? (double)(t1 - t0) * 1e-3 : -1.0;
+      const unsigned long long t1 = b->h_t[b->K + k];
+      latency_us_k[k] = (t1 >= t_start && t_start != ~0ull) ? (double)(t1 - t_start) * 1e-3 : -1.0;
     }
     if (st != BDSS_OK && worst == BDSS_OK) worst = (bdss_status)st;
   }
