@@ -132,9 +132,11 @@ bdss_status bdss_factor(bdss_handle h, const double *A_diag, const double *A_sub
  * Solve with the stored factors (Algorithm 7): upward RHS reduction
  * y_j = L_j^{-1} b_j, b_s -= W^T y (Algorithm 5), the top solve, then the
  * downward back-substitution x_j = L_j^{-T}(y_j - W_L x_{j-1} - W_R x_{j+1})
- * (Algorithms 6 and 2).  1 <= d <= d_max.  X may equal B (in place); otherwise
- * B is not modified.  In the mixed modes this runs the refinement loop and
- * fills info->iters and info->backward_err.
+ * (Algorithms 6 and 2).  1 <= d <= d_max.  In FP64, X may equal B (in
+ * place); otherwise B is not modified.  In the mixed modes this runs the
+ * refinement loop, which reads B again for every residual, so X must differ
+ * from B (else BDSS_ERR_INVALID_ARG); it fills info->iters and
+ * info->backward_err.
  */
 bdss_status bdss_solve(bdss_handle h, const double *B, double *X, int32_t d, bdss_info *info);
 
