@@ -66,7 +66,8 @@ typedef enum {
   BDSS_ERR_CUDA = 5,            /* a CUDA runtime call failed */
   BDSS_ERR_TIMEOUT = 6,         /* a device-side wait exceeded its time limit */
   BDSS_ERR_NO_CONVERGENCE = 7,  /* mixed precision: refinement did not reach the target */
-  BDSS_ERR_UNSUPPORTED = 8      /* a size or mode this build does not implement */
+  BDSS_ERR_UNSUPPORTED = 8,     /* a size or mode this build does not implement */
+  BDSS_ERR_GUARD = 9            /* debug: a workspace guard band was overwritten */
 } bdss_status;
 
 typedef enum {
@@ -95,9 +96,15 @@ typedef enum {
   BDSS_OPT_MAX_REFINE = 2,      /* mixed precision: refinement step limit (default 10) */
   BDSS_OPT_TARGET_BERR_E18 = 3, /* mixed precision: target backward error x 1e18
                                    (default 10000 = 1e-14) */
-  BDSS_OPT_DEBUG_SKIP_ARRIVE = 4 /* test hook: CTA 0 skips its arrival at the given
+  BDSS_OPT_DEBUG_SKIP_ARRIVE = 4, /* test hook: CTA 0 skips its arrival at the given
                                    grid barrier (1-based; 0 = off) so that the waits
                                    of the others run out and BDSS_ERR_TIMEOUT results */
+  BDSS_OPT_DEBUG_GUARDS = 5,    /* 1: after every call, check the guard band (256 bytes
+                                   of a fixed pattern) after each workspace buffer;
+                                   an overwritten band gives BDSS_ERR_GUARD */
+  BDSS_OPT_DEBUG_CORRUPT_GUARD = 6 /* test hook: overwrite, from the host, one byte of
+                                   the guard band of workspace buffer `value` (1-based,
+                                   allocation order) to exercise the check */
 } bdss_option;
 
 /*
@@ -168,6 +175,12 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
 /* Number of grid barriers / kernel launches the last factor or solve issued
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
+
+/* Test hook: the k-th device or page-locked allocation of every following
+ * bdss_create (counted per call, 1-based) fails as if the memory were
+ * exhausted; 0 turns it off.  bdss_create must then return BDSS_ERR_ALLOC
+ * having freed what it had allocated. */
+bdss_status bdss_debug_fail_alloc(int32_t k);
 
 /* Launch configuration the handle chose at creation (host pointers, any may
  * be NULL): resident CTAs per SM of its persistent kernel (from the

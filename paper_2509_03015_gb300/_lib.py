@@ -13,10 +13,11 @@ BDSS_OK = 0
 STATUS_NAMES = {
     0: "BDSS_OK", 1: "BDSS_ERR_INVALID_ARG", 2: "BDSS_ERR_NOT_SPD", 3: "BDSS_ERR_NOT_FACTORED",
     4: "BDSS_ERR_ALLOC", 5: "BDSS_ERR_CUDA", 6: "BDSS_ERR_TIMEOUT", 7: "BDSS_ERR_NO_CONVERGENCE",
-    8: "BDSS_ERR_UNSUPPORTED",
+    8: "BDSS_ERR_UNSUPPORTED", 9: "BDSS_ERR_GUARD",
 }
 PRECISIONS = {"fp64": 0, "fp32_ir": 1, "tf32_ir": 2}
-OPTIONS = {"timeout_ms": 0, "persistent": 1, "max_refine": 2, "target_berr_e18": 3, "debug_skip_arrive": 4}
+OPTIONS = {"timeout_ms": 0, "persistent": 1, "max_refine": 2, "target_berr_e18": 3, "debug_skip_arrive": 4,
+           "debug_guards": 5, "debug_corrupt_guard": 6}
 
 
 class bdss_info(ctypes.Structure):
@@ -38,6 +39,7 @@ SIGNATURES = {
     "bdss_last_launch_stats": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bdss_last_trace": (_i32, [_vp, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32)]),
     "bdss_get_launch_config": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "bdss_debug_fail_alloc": (_i32, [_i32]),
     "bdss_destroy": (_i32, [_vp]),
     "bdss_status_string": (ctypes.c_char_p, [_i32]),
     "bdss_last_cuda_error": (ctypes.c_char_p, []),

@@ -8,7 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
+#include <vector>
 
 #include "../../include/bdss.h"
 #include "bdss_launch.h"
@@ -56,7 +58,49 @@ struct bdss_ctx {
   int64_t barriers = 0;
   int trace_count = 0;               // barrier stamps of the last persistent launch
   long long trace[kTraceSlots] = {};
+  // guard bands after every workspace buffer (checked with the debug option)
+  struct Guard { void *base; size_t bytes; };
+  std::vector<Guard> guards;
+  int debug_guards = 0;
 };
+
+// Workspace guard bands: kGuardBytes of kGuardByte after each buffer.
+static constexpr size_t kGuardBytes = 256;
+static constexpr unsigned char kGuardByte = 0xA5;
+
+// Test hook: the k-th allocation of each following bdss_create fails (0 = off).
+static std::atomic<int> g_fail_alloc{0};
+static thread_local int t_alloc_count = 0;
+
+static bool inject_alloc_failure() {
+  const int k = g_fail_alloc.load();
+  return k > 0 && ++t_alloc_count == k;
+}
+
+// Device workspace with a guard band after it.
+static bool ws_alloc(bdss_ctx *h, void **p, size_t bytes) {
+  *p = nullptr;
+  if (inject_alloc_failure()) return false;
+  if (cudaMalloc(p, bytes + kGuardBytes) != cudaSuccess) {
+    *p = nullptr;
+    return false;
+  }
+  h->guards.push_back({*p, bytes});
+  return cudaMemset(static_cast<char *>(*p) + bytes, kGuardByte, kGuardBytes) == cudaSuccess;
+}
+
+// All guard bands intact?  (Synchronous copies; debug option only.)
+static bool guards_intact(const bdss_ctx *h) {
+  unsigned char buf[kGuardBytes];
+  for (const auto &g : h->guards) {
+    if (cudaMemcpy(buf, static_cast<const char *>(g.base) + g.bytes, kGuardBytes, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return false;
+    for (size_t i = 0; i < kGuardBytes; ++i)
+      if (buf[i] != kGuardByte) return false;
+  }
+  return true;
+}
 
 static constexpr int kLogdetGrid = 256;
 
@@ -109,6 +153,7 @@ static bdss_status finish(bdss_ctx *h, bdss_info *info) {
     info->level = h->hst->level;
     info->block = h->hst->block;
   }
+  if (h->debug_guards && !guards_intact(h)) return BDSS_ERR_GUARD;
   return (bdss_status)st;
 }
 
@@ -229,6 +274,7 @@ const char *bdss_status_string(bdss_status s) {
     case BDSS_ERR_TIMEOUT: return "device wait timed out";
     case BDSS_ERR_NO_CONVERGENCE: return "refinement did not converge";
     case BDSS_ERR_UNSUPPORTED: return "unsupported size or mode";
+    case BDSS_ERR_GUARD: return "a workspace guard band was overwritten";
   }
   return "unknown status";
 }
@@ -293,25 +339,26 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
   }
   const size_t nn = (size_t)n * n;
   const size_t slots = (size_t)(h->plan.off[h->plan.L] > 0 ? h->plan.off[h->plan.L] : 1);
-  bool ok = cudaMalloc(&h->Ld, (size_t)N * nn * esz) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->Wb, slots * nn * esz) == cudaSuccess;
-  if (h->large) ok = ok && cudaMalloc(&h->Eb, slots * nn * esz) == cudaSuccess;
-  ok = ok && cudaMalloc((void **)&h->Ltop, nn * sizeof(double)) == cudaSuccess;
-  ok = ok && cudaMalloc((void **)&h->partial, kLogdetGrid * sizeof(double)) == cudaSuccess;
-  ok = ok && cudaMalloc((void **)&h->dst, sizeof(DevStatus)) == cudaSuccess;
-  ok = ok && cudaMallocHost((void **)&h->hst, sizeof(DevStatus)) == cudaSuccess;
+  t_alloc_count = 0;
+  bool ok = ws_alloc(h, &h->Ld, (size_t)N * nn * esz);
+  ok = ok && ws_alloc(h, &h->Wb, slots * nn * esz);
+  if (h->large) ok = ok && ws_alloc(h, &h->Eb, slots * nn * esz);
+  ok = ok && ws_alloc(h, (void **)&h->Ltop, nn * sizeof(double));
+  ok = ok && ws_alloc(h, (void **)&h->partial, kLogdetGrid * sizeof(double));
+  ok = ok && ws_alloc(h, (void **)&h->dst, sizeof(DevStatus));
+  ok = ok && !inject_alloc_failure() && cudaMallocHost((void **)&h->hst, sizeof(DevStatus)) == cudaSuccess;
   if (ok && h->large && prec == BDSS_TF32_IR && n % 4 == 0) {
     // tensor-core Schur tiles read W^T rows of Wb through TMA
     CUtensorMap map;
     cudaError_t em = make_w_tensor_map(&map, (const float *)h->Wb, (long long)slots * n, n);
-    ok = em == cudaSuccess && cudaMalloc((void **)&h->d_tmap, sizeof(CUtensorMap)) == cudaSuccess &&
+    ok = em == cudaSuccess && ws_alloc(h, (void **)&h->d_tmap, sizeof(CUtensorMap)) &&
          cudaMemcpy(h->d_tmap, &map, sizeof(CUtensorMap), cudaMemcpyHostToDevice) == cudaSuccess;
     h->tf32 = ok ? 1 : 0;
   }
   if (ok && is_mixed(h)) {
     const size_t nd = (size_t)N * n * d_max;
-    ok = cudaMalloc((void **)&h->Y32, nd * sizeof(float)) == cudaSuccess;
-    ok = ok && cudaMalloc((void **)&h->R32, nd * sizeof(float)) == cudaSuccess;
+    ok = ws_alloc(h, (void **)&h->Y32, nd * sizeof(float));
+    ok = ok && ws_alloc(h, (void **)&h->R32, nd * sizeof(float));
   }
   if (!ok) {
     cudaGetLastError();  // clear the allocation error
@@ -346,6 +393,17 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
       if (value < 0) return BDSS_ERR_INVALID_ARG;
       h->skip_barrier = (int)value;
       return BDSS_OK;
+    case BDSS_OPT_DEBUG_GUARDS:
+      if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
+      h->debug_guards = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_DEBUG_CORRUPT_GUARD: {
+      // test hook: overwrite one byte of buffer `value`'s guard band from the host
+      if (value < 1 || value > (int64_t)h->guards.size()) return BDSS_ERR_INVALID_ARG;
+      const auto &g = h->guards[(size_t)value - 1];
+      if (cudaMemset(static_cast<char *>(g.base) + g.bytes, 0, 1) != cudaSuccess) return cuda_fail(cudaGetLastError());
+      return BDSS_OK;
+    }
   }
   return BDSS_ERR_INVALID_ARG;
 }
@@ -597,6 +655,12 @@ bdss_status bdss_tc_selftest(double *max_rel_err) {
   cudaError_t e = run_tc_selftest(max_rel_err, &st);
   if (e != cudaSuccess) return cuda_fail(e);
   return (bdss_status)st;
+}
+
+bdss_status bdss_debug_fail_alloc(int32_t k) {
+  if (k < 0) return BDSS_ERR_INVALID_ARG;
+  g_fail_alloc.store(k);
+  return BDSS_OK;
 }
 
 bdss_status bdss_get_launch_config(bdss_handle h, int32_t *ctas_per_sm, int32_t *sm_count, int64_t *smem_bytes) {

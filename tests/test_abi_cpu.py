@@ -48,10 +48,11 @@ def test_no_cuda_symbols_leak_into_abi(lib):
 
 
 def test_status_strings(lib):
-    for code in range(0, 9):
+    for code in range(0, 10):
         s = lib.bdss_status_string(code)
         assert s and isinstance(s, bytes)
     assert lib.bdss_status_string(0) == b"ok"
+    assert b"guard" in lib.bdss_status_string(9)
 
 
 def test_host_argument_checks(lib):
@@ -74,6 +75,8 @@ def test_host_argument_checks(lib):
     assert lib.bdss_solve(None, None, None, 1, ctypes.byref(info)) == 1
     out = ctypes.c_double()
     assert lib.bdss_logdet(None, ctypes.byref(out)) == 1
+    assert lib.bdss_debug_fail_alloc(-1) == 1
+    assert lib.bdss_debug_fail_alloc(0) == 0
 
 
 def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
