@@ -6,10 +6,11 @@
 // that form level l+1.  Storage (T = double or float):
 //   Ld   : N x n x n.  Slot of original block i.  After factoring, the slot of
 //          every eliminated block holds its Cholesky factor L (lower
-//          triangle; the diagonal holds 1 / L_kk), and the slot of every
-//          separator holds its updated diagonal block (lower triangle) until
-//          it is eliminated.  Block 0 is the top block; its FP64 factor is in
-//          Ltop (same convention).
+//          triangle; the diagonal holds 1 / L_kk) -- in FP32, L^{-1} with the
+//          same diagonal (kStoreInverse) -- and the slot of every separator
+//          holds its updated diagonal block (lower triangle) until it is
+//          eliminated.  Block 0 is the top block; its FP64 factor is in Ltop
+//          (same convention).
 //   Wb   : coupling slots, region l = [off_l, off_l + N_l - 1).  Slot k of
 //          region l couples level-l positions k and k+1.  Region 0 is written
 //          only (its couplings are the caller's A_sub); region l >= 1 first
