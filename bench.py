@@ -257,6 +257,35 @@ def other_workloads(dev, stream, world, max_over_ranks, args):
     return res
 
 
+# Factor + solve times (ms) of the paper's BlockDSS on an H200 (FP64, d = 1):
+# Table 1 (N n = 262,144) and the Kalman-smoother instance of Sec. 4.2
+# (factor + solve; its "Init" phase excluded).  Another machine: context only.
+PAPER_H200_MS = {(1024, 256): 61.72 + 21.70, (2048, 128): 41.91 + 30.86, (4096, 64): 12.65 + 6.84,
+                 (8192, 32): 7.95 + 4.36, (100, 256): 13.3 + 8.6}
+
+
+def paper_shapes(dev, stream, max_over_ranks):
+    """The paper's own problem shapes on this GPU, FP64 factor + solve with
+    d = 1 (synthetic Kalman-type blocks: the paper's generators are not
+    specified); for n = 256 also the FP32 and TF32 refinement paths."""
+    import torch
+
+    from paper_2509_03015_gb300 import Solver
+    res = {}
+    for (N, n), ref in PAPER_H200_MS.items():
+        s = inputs.kalman_btd(N, n, max(1, n // 2), 1, 0.95, 0)
+        Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
+        X = torch.empty_like(B)
+        entry = {"paper_blockdss_h200_ms": ref}
+        for prec in (("fp64", "fp32_ir", "tf32_ir") if n == 256 else ("fp64",)):
+            sol = Solver(N, n, d_max=1, precision=prec, stream=stream)
+            sol.factor_solve(Ad, As, B, X)
+            entry[prec + "_ms"] = _timed(lambda: sol.factor_solve(Ad, As, B, X), 3, stream, max_over_ranks)
+            sol.close()
+        res[f"N{N}-n{n}-d1"] = entry
+    return res
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -491,6 +520,7 @@ def main():
 
     if not args.no_extras and args.N is None:
         out["workloads"] = other_workloads(dev, stream, world, max_over_ranks, args)
+        out["paper_shapes"] = paper_shapes(dev, stream, max_over_ranks)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s)
