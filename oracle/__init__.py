@@ -15,6 +15,8 @@ What it computes (all FP64, on the host):
   schur_partition  the separator/interior permutation of Sec. 3.1 (Eq. 2-4)
                    and the reduced system of Eq. 5, densely (numpy).
   tally            flop counts of the block-Thomas sweep.
+  kalman_assemble  the Kalman-smoother Hessian blocks and right-hand side of
+                   Sec. 4.2 from (G_k, H_k, Q_k^{-1}, R_k^{-1}, z_k, zeta_k).
 
 Pins (tests/test_oracle_pins.py) tie each function to something other than
 itself: dense LAPACK Cholesky on tiny inputs, the closed form of
@@ -294,3 +296,31 @@ def schur_partition(A_diag, A_sub, B, separators):
     else:
         S, b_hat = A_ll, B_l
     return S, b_hat, A_uu, A_lu, A_ll
+
+
+def kalman_assemble(G, H, Qinv, Rinv, z, zeta=None):
+    """Normal equations of the MAP Kalman smoother (Sec. 4.2, "Kalman Smoothing
+    Experiment"), blocks 0-based: step k has transition G[k] (G[0] enters only
+    through zeta[0] = G_1 x_0), observation H[k], precisions Qinv[k], Rinv[k],
+    measurement z[k].  With G_{N+1} = 0:
+      A_kk      = Qinv[k] + G[k+1]^T Qinv[k+1] G[k+1] + H[k]^T Rinv[k] H[k]
+      A_{k+1,k} = -Qinv[k+1] G[k+1]
+      b_k       = H[k]^T Rinv[k] z[k] + Qinv[k] zeta[k] - G[k+1]^T Qinv[k+1] zeta[k+1]
+    (the right-hand side read from G^T Q^{-1} zeta with G the block-bidiagonal
+    state operator).  Returns (A_diag, A_sub, B) with B of shape (N, n, 1)."""
+    G, H, Qinv, Rinv, z = (np.asarray(a, dtype=np.float64) for a in (G, H, Qinv, Rinv, z))
+    N, n = G.shape[0], G.shape[1]
+    zeta = np.zeros((N, n)) if zeta is None else np.asarray(zeta, dtype=np.float64)
+    A_diag = np.empty((N, n, n))
+    A_sub = np.empty((max(N - 1, 0), n, n))
+    B = np.empty((N, n, 1))
+    for k in range(N):
+        Akk = Qinv[k] + H[k].T @ Rinv[k] @ H[k]
+        b = H[k].T @ (Rinv[k] @ z[k]) + Qinv[k] @ zeta[k]
+        if k + 1 < N:
+            Akk = Akk + G[k + 1].T @ Qinv[k + 1] @ G[k + 1]
+            A_sub[k] = -(Qinv[k + 1] @ G[k + 1])
+            b = b - G[k + 1].T @ (Qinv[k + 1] @ zeta[k + 1])
+        A_diag[k] = Akk
+        B[k, :, 0] = b
+    return A_diag, A_sub, B
