@@ -182,8 +182,8 @@ def _timed(fn, reps, stream, max_over_ranks):
 def other_workloads(dev, stream, world, max_over_ranks, args):
     """The other hot-path workloads on the same GPU: the N=4096, n=256, d=16
     mixed-precision system (FP32 + refinement vs FP64), the 512-instance
-    uneven MPC batch in one launch, and forward + adjoint backward at
-    N=2048, n=32, d=8."""
+    uneven MPC batch in one launch, forward + adjoint backward at
+    N=2048, n=32, d=8, and the on-device Kalman-smoother assembly."""
     import torch
 
     from paper_2509_03015_gb300 import BatchSolver, Solver, block_tri_solve
@@ -254,7 +254,42 @@ def other_workloads(dev, stream, world, max_over_ranks, args):
     fwd_bwd()
     ms = _timed(fwd_bwd, reps, stream, max_over_ranks)
     res[name] = {"value": world * 1e3 / ms, "unit": "systems/s (forward + backward)", "ms_per_step": ms}
+    # -- Kalman-smoother assembly on the device ---------------------------------------
+    res["kalman-assembly-N16384-n64-m32"] = kalman_assembly(dev, stream, world, max_over_ranks, reps)
     return res
+
+
+def kalman_assembly(dev, stream, world, max_over_ranks, reps, N=16384, n=64, m=32):
+    """Kalman-smoother normal equations assembled on the device from a
+    per-step model (G_k, H_k, Q_k^-1, R_k^-1, z_k, zeta_k), then factored and
+    solved: the assembly alone and the whole smoother step.  FLOPs per step k:
+    2n^3 (Q^-1 G) + 2m^2 n (R^-1 H) + 2m n^2 (H^T U) + 2n^3 (G^T A_sub) plus
+    the matrix-vector products of the right-hand side."""
+    import torch
+
+    from paper_2509_03015_gb300 import Solver, kalman_assemble
+    mod = inputs.kalman_model(N, n, m, seed=0)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in mod.items()}
+    del mod
+    args = (d["G"], d["H"], d["Qinv"], d["Rinv"], d["z"], d["zeta"])
+    A_diag, A_sub, B = kalman_assemble(*args, stream=stream)
+    ms = _timed(lambda: kalman_assemble(*args, stream=stream), reps, stream, max_over_ranks)
+    flops = N * (4 * n ** 3 + 2 * m * m * n + 2 * m * n * n + 2 * m * m + 2 * n * n + 2 * m * n + 2 * n * n)
+    in_bytes = 8 * N * (2 * n * n + m * n + m * m + m + n)
+    out_bytes = 8 * N * (2 * n * n + n)
+    sol = Solver(N, n, d_max=1, stream=stream)
+
+    def step():
+        Ad, As, Bk = kalman_assemble(*args, stream=stream)
+        return sol.factor_solve(Ad, As, Bk)
+    step()
+    step_ms = _timed(step, reps, stream, max_over_ranks)
+    sol.close()
+    return {"N": N, "n": n, "m": m, "assemble_ms": ms, "value": world * 1e3 / ms, "unit": "assemblies/s",
+            "assemble_gflops": flops / (ms * 1e-3) / 1e9, "flops_per_assembly": flops,
+            "min_dram_bytes": in_bytes + out_bytes,
+            "assemble_plus_factor_solve_ms": step_ms,
+            "note": "FP64; model drawn by inputs.kalman_model(seed 0); outputs allocated per call"}
 
 
 # Factor + solve times (ms) of the paper's BlockDSS on an H200 (FP64, d = 1):

@@ -172,14 +172,39 @@ bdss_status bdss_logdet(bdss_handle h, double *out);
 bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double *X, int32_t d,
                                double *dA_diag, double *dA_sub);
 
+/*
+ * Kalman-smoother normal equations (Sec. 4.2, the smoothing experiment),
+ * assembled on the device from the model of N steps (0-based k):
+ *   A_diag[k]  = Qinv[k] + G[k+1]^T Qinv[k+1] G[k+1] + H[k]^T Rinv[k] H[k]
+ *   A_sub[k]   = -Qinv[k+1] G[k+1]                        (k < N-1)
+ *   B[k]       = H[k]^T Rinv[k] z[k] + Qinv[k] zeta[k] - G[k+1]^T Qinv[k+1] zeta[k+1]
+ * with the G[k+1] terms absent for k = N-1.  G[0] is not read (the prior mean
+ * enters through zeta[0], the prior precision as Qinv[0]).  Layouts, all
+ * row-major FP64 device memory, 16-byte aligned:
+ *   G, Qinv: N x n x n;  H: N x m x n;  Rinv: N x m x m;  z: N x m;
+ *   zeta: N x n, or NULL for zero;  A_diag: N x n x n;  A_sub: (N-1) x n x n
+ *   (may be NULL iff N == 1);  B: N x n x 1, or NULL to assemble the matrix
+ *   only (z is then not read and may be NULL).
+ * The outputs feed bdss_factor / bdss_solve directly.  Sizes: N, n, m >= 1
+ * (else BDSS_ERR_INVALID_ARG); n <= 256, m <= 4096 and N (n/64 rounded up)
+ * (n/64 + m/64 rounded up, + 1) < 2^31 (else BDSS_ERR_UNSUPPORTED).  The call
+ * allocates N (m n + m + n) doubles of stream-ordered workspace on `cuda_stream`
+ * (BDSS_ERR_ALLOC if that fails), runs two kernels and synchronises the stream
+ * before it returns.  Outputs must not overlap inputs.
+ */
+bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, const double *G, const double *H,
+                                 const double *Qinv, const double *Rinv, const double *z,
+                                 const double *zeta, double *A_diag, double *A_sub, double *B,
+                                 void *cuda_stream);
+
 /* Number of grid barriers / kernel launches the last factor or solve issued
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
 
 /* Test hook: the k-th device or page-locked allocation of every following
- * bdss_create (counted per call, 1-based) fails as if the memory were
- * exhausted; 0 turns it off.  bdss_create must then return BDSS_ERR_ALLOC
- * having freed what it had allocated. */
+ * bdss_create or bdss_kalman_assemble (counted per call, 1-based) fails as if
+ * the memory were exhausted; 0 turns it off.  The call must then return
+ * BDSS_ERR_ALLOC having freed what it had allocated. */
 bdss_status bdss_debug_fail_alloc(int32_t k);
 
 /* Launch configuration the handle chose at creation (host pointers, any may

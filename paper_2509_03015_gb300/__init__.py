@@ -12,7 +12,8 @@ from ._lib import BDSSError, load  # noqa: F401
 def __getattr__(name):
     # torch-facing binding, imported lazily so that the C-ABI layer and the
     # input generators load without torch
-    if name in ("Solver", "solve", "BlockTriSolve", "block_tri_solve", "BatchSolver"):
+    if name in ("Solver", "solve", "BlockTriSolve", "block_tri_solve", "BatchSolver",
+                "kalman_assemble"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

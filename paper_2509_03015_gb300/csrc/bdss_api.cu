@@ -14,6 +14,7 @@
 
 #include "../../include/bdss.h"
 #include "bdss_launch.h"
+#include "bdss_kalman.h"
 
 using namespace bdss;
 
@@ -645,6 +646,49 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
   if (d < 1 || d > h->d_max) return BDSS_ERR_INVALID_ARG;
   cudaError_t e = launch_adjoint_grads(h->N, h->n, d, Lambda, X, dA_diag, dA_sub, grid_for(h, h->N) * 2, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return BDSS_OK;
+}
+
+bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, const double *G, const double *H,
+                                 const double *Qinv, const double *Rinv, const double *z,
+                                 const double *zeta, double *A_diag, double *A_sub, double *B,
+                                 void *cuda_stream) {
+  if (N < 1 || n < 1 || m < 1) return BDSS_ERR_INVALID_ARG;
+  if (n > kMaxNLarge || m > 4096 || N > kalman_max_steps(n, m)) return BDSS_ERR_UNSUPPORTED;
+  auto ok_in = [](const void *p) { return p && aligned16(p) && device_memory(p); };
+  if (!ok_in(G) || !ok_in(H) || !ok_in(Qinv) || !ok_in(Rinv) || !ok_in(A_diag)) return BDSS_ERR_INVALID_ARG;
+  if (N > 1 && !ok_in(A_sub)) return BDSS_ERR_INVALID_ARG;
+  if (B && (!ok_in(B) || !ok_in(z))) return BDSS_ERR_INVALID_ARG;
+  if (B && zeta && !ok_in(zeta)) return BDSS_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  KalmanArgs a{};
+  a.N = N;
+  a.n = n;
+  a.m = m;
+  a.G = G;
+  a.H = H;
+  a.Qinv = Qinv;
+  a.Rinv = Rinv;
+  a.z = B ? z : nullptr;
+  a.zeta = B ? zeta : nullptr;
+  a.A_diag = A_diag;
+  a.A_sub = N > 1 ? A_sub : nullptr;
+  a.B = B;
+  const size_t words = (size_t)N * ((size_t)m * n + m + n);
+  void *ws = nullptr;
+  t_alloc_count = 0;
+  if (inject_alloc_failure() || cudaMallocAsync(&ws, words * sizeof(double), s) != cudaSuccess) {
+    cudaGetLastError();
+    return BDSS_ERR_ALLOC;
+  }
+  a.U = static_cast<double *>(ws);
+  a.v = a.U + (size_t)N * m * n;
+  a.w = a.v + (size_t)N * m;
+  cudaError_t e = launch_kalman_assemble(a, s);
+  cudaError_t f = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = f;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e);
   return BDSS_OK;
 }

@@ -19,6 +19,9 @@ Generators:
                     the parity tests so that an indexing mistake cannot hide
                     behind repeated blocks.
   tridiag_121    -- n = 1, A = tridiag(-1, 2, -1), B = 1.
+  kalman_model   -- a time-varying state-space model (G_k, H_k, Q_k^-1, R_k^-1,
+                    z_k, zeta_k), the input of the on-device assembly of the
+                    Kalman-smoother normal equations.
 """
 from __future__ import annotations
 
@@ -95,6 +98,26 @@ def kalman_btd(N: int, n: int, m: int, d: int, rho: float, seed: int, with_W: bo
     if with_W:
         out["W"] = rng.standard_normal((N * n, d)).reshape(N, n, d)
     return out
+
+
+def kalman_model(N: int, n: int, m: int, seed: int, g_scale: float = 0.5):
+    """Per-step model with every block distinct, drawn from
+    numpy.random.default_rng(seed) in the order G, H, M_Q, M_R, z, zeta:
+    G_k = g_scale * Gaussian / sqrt(n), H_k = Gaussian / sqrt(n),
+    Qinv_k = M_Q M_Q^T / n + I, Rinv_k = M_R M_R^T / m + I, z_k and zeta_k
+    standard Gaussian.  Returns a dict of C-contiguous float64 arrays with the
+    shapes G, Qinv (N, n, n), H (N, m, n), Rinv (N, m, m), z (N, m),
+    zeta (N, n)."""
+    rng = np.random.default_rng(seed)
+    G = g_scale * rng.standard_normal((N, n, n)) / math.sqrt(n)
+    H = rng.standard_normal((N, m, n)) / math.sqrt(n)
+    Mq = rng.standard_normal((N, n, n))
+    Mr = rng.standard_normal((N, m, m))
+    z = rng.standard_normal((N, m))
+    zeta = rng.standard_normal((N, n))
+    Qinv = np.matmul(Mq, Mq.transpose(0, 2, 1)) / n + np.eye(n)
+    Rinv = np.matmul(Mr, Mr.transpose(0, 2, 1)) / m + np.eye(m)
+    return dict(G=G, H=H, Qinv=np.ascontiguousarray(Qinv), Rinv=np.ascontiguousarray(Rinv), z=z, zeta=zeta)
 
 
 def workload(name: str, with_W: bool = False):

@@ -200,6 +200,35 @@ def block_tri_solve(A_diag, A_sub, B):
     return BlockTriSolve.apply(A_diag, A_sub, B)
 
 
+def kalman_assemble(G, H, Qinv, Rinv, z=None, zeta=None, stream=None):
+    """Kalman-smoother normal equations (Sec. 4.2) assembled on the GPU:
+    returns (A_diag, A_sub, B) ready for Solver.factor_solve, B of shape
+    (N, n, 1), or None when z is None (matrix only).  G, Qinv: (N, n, n);
+    H: (N, m, n); Rinv: (N, m, m); z: (N, m); zeta: (N, n) or None for zero.
+    G[0] is not read."""
+    lib = _lib.load()
+    N, n, _ = G.shape
+    m = H.shape[1]
+    _check_tensor(G, "G", (N, n, n))
+    _check_tensor(H, "H", (N, m, n))
+    _check_tensor(Qinv, "Qinv", (N, n, n))
+    _check_tensor(Rinv, "Rinv", (N, m, m))
+    if z is not None:
+        _check_tensor(z, "z", (N, m))
+        if zeta is not None:
+            _check_tensor(zeta, "zeta", (N, n))
+    dev = G.device
+    A_diag = torch.empty((N, n, n), dtype=torch.float64, device=dev)
+    A_sub = torch.empty((max(N - 1, 0), n, n), dtype=torch.float64, device=dev)
+    B = torch.empty((N, n, 1), dtype=torch.float64, device=dev) if z is not None else None
+    stream = stream if stream is not None else torch.cuda.current_stream(dev)
+    st = lib.bdss_kalman_assemble(N, n, m, _ptr(G), _ptr(H), _ptr(Qinv), _ptr(Rinv), _ptr(z), _ptr(zeta),
+                                  _ptr(A_diag), _ptr(A_sub if N > 1 else None), _ptr(B),
+                                  ctypes.c_void_p(stream.cuda_stream))
+    _lib.check(st, "bdss_kalman_assemble")
+    return A_diag, A_sub, B
+
+
 class BatchSolver:
     """K independent FP64 systems of uneven (N_k, n_k), factored and solved in
     one launch (device work queue).  `systems` is a list of (A_diag, A_sub,
