@@ -302,10 +302,12 @@ PAPER_H200_MS = {(1024, 256): 61.72 + 21.70, (2048, 128): 41.91 + 30.86, (4096, 
 def paper_shapes(dev, stream, max_over_ranks):
     """The paper's own problem shapes on this GPU, FP64 factor + solve with
     d = 1 (synthetic Kalman-type blocks: the paper's generators are not
-    specified); for n = 256 also the FP32 and TF32 refinement paths."""
+    specified); for n = 256 also the FP32 and TF32 refinement paths.  Then the
+    neuroscience-shaped Kalman instance (N = 100, n = 256, m = 1024) assembled
+    on the device from a synthetic model and solved at each precision."""
     import torch
 
-    from paper_2509_03015_gb300 import Solver
+    from paper_2509_03015_gb300 import Solver, kalman_assemble
     res = {}
     for (N, n), ref in PAPER_H200_MS.items():
         s = inputs.kalman_btd(N, n, max(1, n // 2), 1, 0.95, 0)
@@ -318,6 +320,21 @@ def paper_shapes(dev, stream, max_over_ranks):
             entry[prec + "_ms"] = _timed(lambda: sol.factor_solve(Ad, As, B, X), 3, stream, max_over_ranks)
             sol.close()
         res[f"N{N}-n{n}-d1"] = entry
+    # the neuroscience-shaped instance assembled on the device (diagonal R)
+    mod = inputs.kalman_neuro_model()
+    N, n, m = mod["H"].shape[0], mod["H"].shape[2], mod["H"].shape[1]
+    d = {k: torch.from_numpy(v).to(dev) for k, v in mod.items()}
+    args = (d["G"], d["H"], d["Qinv"], d["Rinv"], d["z"], d["zeta"])
+    Ad, As, B = kalman_assemble(*args, stream=stream)
+    entry = {"paper_blockdss_h200_ms": PAPER_H200_MS[(N, n)], "m": m,
+             "assemble_ms": _timed(lambda: kalman_assemble(*args, stream=stream), 3, stream, max_over_ranks)}
+    X = torch.empty_like(B)
+    for prec in ("fp64", "fp32_ir", "tf32_ir"):
+        sol = Solver(N, n, d_max=1, precision=prec, stream=stream)
+        sol.factor_solve(Ad, As, B, X)
+        entry[prec + "_ms"] = _timed(lambda: sol.factor_solve(Ad, As, B, X), 3, stream, max_over_ranks)
+        sol.close()
+    res[f"kalman-neuro-N{N}-n{n}-m{m}-d1"] = entry
     return res
 
 

@@ -181,21 +181,23 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
  * with the G[k+1] terms absent for k = N-1.  G[0] is not read (the prior mean
  * enters through zeta[0], the prior precision as Qinv[0]).  Layouts, all
  * row-major FP64 device memory, 16-byte aligned:
- *   G, Qinv: N x n x n;  H: N x m x n;  Rinv: N x m x m;  z: N x m;
+ *   G, Qinv: N x n x n;  H: N x m x n;  Rinv: N x m x m, or, with
+ *   rinv_diagonal = 1, N x m holding the diagonals of diagonal R[k]^-1 (the
+ *   R_k^-1 H_k product is then a row scaling);  z: N x m;
  *   zeta: N x n, or NULL for zero;  A_diag: N x n x n;  A_sub: (N-1) x n x n
  *   (may be NULL iff N == 1);  B: N x n x 1, or NULL to assemble the matrix
  *   only (z is then not read and may be NULL).
  * The outputs feed bdss_factor / bdss_solve directly.  Sizes: N, n, m >= 1
- * (else BDSS_ERR_INVALID_ARG); n <= 256, m <= 4096 and N (n/64 rounded up)
+ * and rinv_diagonal 0 or 1 (else BDSS_ERR_INVALID_ARG); n <= 256, m <= 4096 and N (n/64 rounded up)
  * (n/64 + m/64 rounded up, + 1) < 2^31 (else BDSS_ERR_UNSUPPORTED).  The call
  * allocates N (m n + m + n) doubles of stream-ordered workspace on `cuda_stream`
  * (BDSS_ERR_ALLOC if that fails), runs two kernels and synchronises the stream
  * before it returns.  Outputs must not overlap inputs.
  */
-bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, const double *G, const double *H,
-                                 const double *Qinv, const double *Rinv, const double *z,
-                                 const double *zeta, double *A_diag, double *A_sub, double *B,
-                                 void *cuda_stream);
+bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, int32_t rinv_diagonal,
+                                 const double *G, const double *H, const double *Qinv,
+                                 const double *Rinv, const double *z, const double *zeta,
+                                 double *A_diag, double *A_sub, double *B, void *cuda_stream);
 
 /* Number of grid barriers / kernel launches the last factor or solve issued
  * (host pointers, either may be NULL). */

@@ -307,8 +307,12 @@ def kalman_assemble(G, H, Qinv, Rinv, z, zeta=None):
       A_{k+1,k} = -Qinv[k+1] G[k+1]
       b_k       = H[k]^T Rinv[k] z[k] + Qinv[k] zeta[k] - G[k+1]^T Qinv[k+1] zeta[k+1]
     (the right-hand side read from G^T Q^{-1} zeta with G the block-bidiagonal
-    state operator).  Returns (A_diag, A_sub, B) with B of shape (N, n, 1)."""
+    state operator).  Rinv of shape (N, m) holds diagonal precisions (the
+    neuroscience instance of Sec. 4.2 has a diagonal R).  Returns
+    (A_diag, A_sub, B) with B of shape (N, n, 1)."""
     G, H, Qinv, Rinv, z = (np.asarray(a, dtype=np.float64) for a in (G, H, Qinv, Rinv, z))
+    if Rinv.ndim == 2:
+        Rinv = np.stack([np.diag(r) for r in Rinv])
     N, n = G.shape[0], G.shape[1]
     zeta = np.zeros((N, n)) if zeta is None else np.asarray(zeta, dtype=np.float64)
     A_diag = np.empty((N, n, n))

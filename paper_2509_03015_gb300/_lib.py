@@ -56,7 +56,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                          ctypes.POINTER(_vp), _vp, _info_p]),
     "bdss_factor_solve_noalloc": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _info_p]),
-    "bdss_kalman_assemble": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bdss_kalman_assemble": (_i32, [_i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -650,11 +650,11 @@ bdss_status bdss_adjoint_grads(bdss_handle h, const double *Lambda, const double
   return BDSS_OK;
 }
 
-bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, const double *G, const double *H,
-                                 const double *Qinv, const double *Rinv, const double *z,
-                                 const double *zeta, double *A_diag, double *A_sub, double *B,
-                                 void *cuda_stream) {
-  if (N < 1 || n < 1 || m < 1) return BDSS_ERR_INVALID_ARG;
+bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, int32_t rinv_diagonal,
+                                 const double *G, const double *H, const double *Qinv,
+                                 const double *Rinv, const double *z, const double *zeta,
+                                 double *A_diag, double *A_sub, double *B, void *cuda_stream) {
+  if (N < 1 || n < 1 || m < 1 || (rinv_diagonal != 0 && rinv_diagonal != 1)) return BDSS_ERR_INVALID_ARG;
   if (n > kMaxNLarge || m > 4096 || N > kalman_max_steps(n, m)) return BDSS_ERR_UNSUPPORTED;
   auto ok_in = [](const void *p) { return p && aligned16(p) && device_memory(p); };
   if (!ok_in(G) || !ok_in(H) || !ok_in(Qinv) || !ok_in(Rinv) || !ok_in(A_diag)) return BDSS_ERR_INVALID_ARG;
@@ -666,6 +666,7 @@ bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, const double *
   a.N = N;
   a.n = n;
   a.m = m;
+  a.rinv_diag = rinv_diagonal;
   a.G = G;
   a.H = H;
   a.Qinv = Qinv;

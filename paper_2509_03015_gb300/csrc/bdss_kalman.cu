@@ -8,8 +8,9 @@
 //   b_k       = H_k^T Rinv_k z_k + Qinv_k zeta_k - G_{k+1}^T Qinv_{k+1} zeta_{k+1}
 // Two launches, each a flat grid of (step, task) CTAs whose tasks of one step
 // are adjacent so that step's operands are shared through L2:
-//   products  A_{k+1,k} tiles (-Qinv G), U_k = Rinv_k H_k tiles, and the
-//             vectors v_k = Rinv_k z_k, w_k = Qinv_k zeta_k;
+//   products  A_{k+1,k} tiles (-Qinv G), U_k = Rinv_k H_k tiles (a row
+//             scaling when Rinv_k is diagonal), and the vectors
+//             v_k = Rinv_k z_k, w_k = Qinv_k zeta_k;
 //   diagonal  A_kk tiles = Qinv_k + H_k^T U_k - G_{k+1}^T A_{k+1,k}, and b_k.
 // All arithmetic is FP64, 64 x 64 output tiles through gemm_nt_tile.
 #include "bdss_large.cuh"
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(kThreads) k_kalman_products(KalmanArgs a) {
   const int tasks = nt * nt + mt * nt + 1;
   const long long k = (long long)blockIdx.x / tasks;
   const int t = (int)((long long)blockIdx.x - k * tasks);
-  const long long nn = (long long)n * n, mn = (long long)m * n, mm = (long long)m * m;
+  const long long nn = (long long)n * n, mn = (long long)m * n;
+  const long long mm = a.rinv_diag ? (long long)m : (long long)m * m;  // Rinv stride per step
   double acc[4][4] = {};
   if (t < nt * nt) {
     if (k + 1 >= a.N) return;
@@ -53,6 +55,15 @@ __global__ void __launch_bounds__(kThreads) k_kalman_products(KalmanArgs a) {
     store_tile(a.A_sub + k * nn, n, n, n, r0, c0, acc, -1.0, nullptr);
   } else if (t < nt * nt + mt * nt) {
     const int u = t - nt * nt, r0 = (u / nt) * kTile, c0 = (u % nt) * kTile;
+    if (a.rinv_diag) {
+      const double *rk = a.Rinv + k * mm, *Hk = a.H + k * mn;
+      double *Uk = a.U + k * mn;
+      for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = r0 + e / kTile, c = c0 + e % kTile;
+        if (r < m && c < n) Uk[(long long)r * n + c] = rk[r] * Hk[(long long)r * n + c];
+      }
+      return;
+    }
     const View<double> R{a.Rinv + k * mm, m, 1, m, m};         // (r, j) -> Rinv_k[r][j]
     const View<double> Ht{a.H + k * mn, 1, n, n, m};           // (c, j) -> H_k[j][c]
     gemm_nt_tile(acc, R, r0, Ht, c0, m, sA, sB);
@@ -62,7 +73,10 @@ __global__ void __launch_bounds__(kThreads) k_kalman_products(KalmanArgs a) {
     const double *Rk = a.Rinv + k * mm, *zk = a.z + k * m;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       double s = 0.0;
-      for (int j = 0; j < m; ++j) s = fma(Rk[(long long)i * m + j], zk[j], s);
+      if (a.rinv_diag)
+        s = Rk[i] * zk[i];
+      else
+        for (int j = 0; j < m; ++j) s = fma(Rk[(long long)i * m + j], zk[j], s);
       a.v[k * m + i] = s;
     }
     const double *Qk = a.Qinv + k * nn, *ek = a.zeta ? a.zeta + k * n : nullptr;

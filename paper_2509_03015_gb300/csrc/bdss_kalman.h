@@ -6,10 +6,11 @@
 namespace bdss {
 
 // Normal equations assembled on the device.  U (N m n), v (N m), w (N n) are
-// workspace; B == nullptr skips the right-hand side.
+// workspace; B == nullptr skips the right-hand side; rinv_diag: Rinv holds
+// only the diagonals (N x m) of diagonal observation precisions.
 struct KalmanArgs {
   long long N;
-  int n, m;
+  int n, m, rinv_diag;
   const double *G, *H, *Qinv, *Rinv, *z, *zeta;
   double *A_diag, *A_sub, *B;
   double *U, *v, *w;

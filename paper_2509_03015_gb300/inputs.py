@@ -22,6 +22,8 @@ Generators:
   kalman_model   -- a time-varying state-space model (G_k, H_k, Q_k^-1, R_k^-1,
                     z_k, zeta_k), the input of the on-device assembly of the
                     Kalman-smoother normal equations.
+  kalman_neuro_model -- the same inputs shaped like the neuroscience instance of
+                    Sec. 4.2 (damped-rotation G, tall H, dense Q, diagonal R).
 """
 from __future__ import annotations
 
@@ -118,6 +120,45 @@ def kalman_model(N: int, n: int, m: int, seed: int, g_scale: float = 0.5):
     Qinv = np.matmul(Mq, Mq.transpose(0, 2, 1)) / n + np.eye(n)
     Rinv = np.matmul(Mr, Mr.transpose(0, 2, 1)) / m + np.eye(m)
     return dict(G=G, H=H, Qinv=np.ascontiguousarray(Qinv), Rinv=np.ascontiguousarray(Rinv), z=z, zeta=zeta)
+
+
+def kalman_neuro_model(N: int = 100, n: int = 256, m: int = 1024, seed: int = 0):
+    """Synthetic stand-in for the neuroscience instance of Sec. 4.2, whose
+    data, damping and covariances are not given.  Drawn from
+    numpy.random.default_rng(seed) in the order rho, theta, H, M, x0, z:
+      G_k = G for k >= 1: block diagonal of n/2 damped 2-D rotations
+            rho_i [[cos t_i, -sin t_i], [sin t_i, cos t_i]],
+            rho_i ~ U(0.95, 0.999), t_i ~ U(0, pi/4); G_0 = I;
+      H_k = H: Gaussian / sqrt(m), m x n with m >= n (well conditioned);
+      Q = 0.05 (M M^T / n + I), dense SPD, Qinv = Q^-1 for every step;
+      R = I (diagonal, larger than Q): Rinv given as its diagonal, (N, m);
+      zeta_0 = G_0 x0 = x0 (the known initial state), zeta_k = 0 after it;
+      z_k standard Gaussian.
+    Returns the arrays of kalman_model, Rinv of shape (N, m)."""
+    if n % 2:
+        raise ValueError("n must be even (2-D rotations)")
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.95, 0.999, n // 2)
+    theta = rng.uniform(0.0, math.pi / 4, n // 2)
+    Hm = rng.standard_normal((m, n)) / math.sqrt(m)
+    M = rng.standard_normal((n, n))
+    x0 = rng.standard_normal(n)
+    z = rng.standard_normal((N, m))
+    Gm = np.zeros((n, n))
+    for i in range(n // 2):
+        c, s_ = math.cos(theta[i]), math.sin(theta[i])
+        Gm[2 * i:2 * i + 2, 2 * i:2 * i + 2] = rho[i] * np.array([[c, -s_], [s_, c]])
+    Qinv1 = np.linalg.inv(0.05 * (M @ M.T / n + np.eye(n)))
+    Qinv1 = 0.5 * (Qinv1 + Qinv1.T)
+    G = np.empty((N, n, n))
+    G[:] = Gm
+    G[0] = np.eye(n)
+    H = np.ascontiguousarray(np.broadcast_to(Hm, (N, m, n)))
+    Qinv = np.ascontiguousarray(np.broadcast_to(Qinv1, (N, n, n)))
+    Rinv = np.ones((N, m))
+    zeta = np.zeros((N, n))
+    zeta[0] = x0
+    return dict(G=G, H=H, Qinv=Qinv, Rinv=Rinv, z=z, zeta=zeta)
 
 
 def workload(name: str, with_W: bool = False):

@@ -204,15 +204,16 @@ def kalman_assemble(G, H, Qinv, Rinv, z=None, zeta=None, stream=None):
     """Kalman-smoother normal equations (Sec. 4.2) assembled on the GPU:
     returns (A_diag, A_sub, B) ready for Solver.factor_solve, B of shape
     (N, n, 1), or None when z is None (matrix only).  G, Qinv: (N, n, n);
-    H: (N, m, n); Rinv: (N, m, m); z: (N, m); zeta: (N, n) or None for zero.
-    G[0] is not read."""
+    H: (N, m, n); Rinv: (N, m, m), or (N, m) for diagonal precisions (their
+    diagonals); z: (N, m); zeta: (N, n) or None for zero.  G[0] is not read."""
     lib = _lib.load()
     N, n, _ = G.shape
     m = H.shape[1]
+    diag = Rinv.dim() == 2
     _check_tensor(G, "G", (N, n, n))
     _check_tensor(H, "H", (N, m, n))
     _check_tensor(Qinv, "Qinv", (N, n, n))
-    _check_tensor(Rinv, "Rinv", (N, m, m))
+    _check_tensor(Rinv, "Rinv", (N, m) if diag else (N, m, m))
     if z is not None:
         _check_tensor(z, "z", (N, m))
         if zeta is not None:
@@ -222,7 +223,7 @@ def kalman_assemble(G, H, Qinv, Rinv, z=None, zeta=None, stream=None):
     A_sub = torch.empty((max(N - 1, 0), n, n), dtype=torch.float64, device=dev)
     B = torch.empty((N, n, 1), dtype=torch.float64, device=dev) if z is not None else None
     stream = stream if stream is not None else torch.cuda.current_stream(dev)
-    st = lib.bdss_kalman_assemble(N, n, m, _ptr(G), _ptr(H), _ptr(Qinv), _ptr(Rinv), _ptr(z), _ptr(zeta),
+    st = lib.bdss_kalman_assemble(N, n, m, int(diag), _ptr(G), _ptr(H), _ptr(Qinv), _ptr(Rinv), _ptr(z), _ptr(zeta),
                                   _ptr(A_diag), _ptr(A_sub if N > 1 else None), _ptr(B),
                                   ctypes.c_void_p(stream.cuda_stream))
     _lib.check(st, "bdss_kalman_assemble")

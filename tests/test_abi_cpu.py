@@ -79,13 +79,14 @@ def test_host_argument_checks(lib):
     assert lib.bdss_debug_fail_alloc(0) == 0
     # Kalman assembly: sizes first, then NULL inputs, all before any CUDA call
     nul = [None] * 10
-    assert lib.bdss_kalman_assemble(0, 8, 4, *nul) == 1
-    assert lib.bdss_kalman_assemble(4, 0, 4, *nul) == 1
-    assert lib.bdss_kalman_assemble(4, 8, 0, *nul) == 1
-    assert lib.bdss_kalman_assemble(4, 257, 4, *nul) == 8
-    assert lib.bdss_kalman_assemble(4, 8, 4097, *nul) == 8
-    assert lib.bdss_kalman_assemble(1 << 31, 64, 64, *nul) == 8
-    assert lib.bdss_kalman_assemble(4, 8, 4, *nul) == 1
+    assert lib.bdss_kalman_assemble(0, 8, 4, 0, *nul) == 1
+    assert lib.bdss_kalman_assemble(4, 0, 4, 0, *nul) == 1
+    assert lib.bdss_kalman_assemble(4, 8, 0, 0, *nul) == 1
+    assert lib.bdss_kalman_assemble(4, 8, 4, 2, *nul) == 1
+    assert lib.bdss_kalman_assemble(4, 257, 4, 0, *nul) == 8
+    assert lib.bdss_kalman_assemble(4, 8, 4097, 1, *nul) == 8
+    assert lib.bdss_kalman_assemble(1 << 31, 64, 64, 0, *nul) == 8
+    assert lib.bdss_kalman_assemble(4, 8, 4, 1, *nul) == 1
 
 
 def test_package_fails_loudly_without_library(tmp_path, monkeypatch):

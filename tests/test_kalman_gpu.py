@@ -84,9 +84,9 @@ def test_rejects_bad_arguments_and_reports_alloc_failure():
     p = [ctypes.c_void_p(t.data_ptr()) for t in (d["G"], d["H"], d["Qinv"], d["Rinv"])]
     tail = [ctypes.c_void_p(d["zeta"].data_ptr()), ctypes.c_void_p(out.data_ptr()),
             ctypes.c_void_p(sub.data_ptr()), ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(None)]
-    assert lib.bdss_kalman_assemble(3, 8, 4, *p, ctypes.c_void_p(zh.data_ptr()), *tail) == 1
-    assert lib.bdss_kalman_assemble(3, 8, 4, *p, ctypes.c_void_p(d["z"].data_ptr()), *tail) == 0
-    assert lib.bdss_kalman_assemble(3, 8, 4097, *p, ctypes.c_void_p(d["z"].data_ptr()), *tail) == 8
+    assert lib.bdss_kalman_assemble(3, 8, 4, 0, *p, ctypes.c_void_p(zh.data_ptr()), *tail) == 1
+    assert lib.bdss_kalman_assemble(3, 8, 4, 0, *p, ctypes.c_void_p(d["z"].data_ptr()), *tail) == 0
+    assert lib.bdss_kalman_assemble(3, 8, 4097, 0, *p, ctypes.c_void_p(d["z"].data_ptr()), *tail) == 8
     assert lib.bdss_debug_fail_alloc(1) == 0
     try:
         with pytest.raises(_lib.BDSSError) as e:
@@ -97,3 +97,33 @@ def test_rejects_bad_arguments_and_reports_alloc_failure():
     A_diag, _, _ = kalman_assemble(d["G"], d["H"], d["Qinv"], d["Rinv"], d["z"])
     rd, _, _ = oracle.kalman_assemble(mod["G"], mod["H"], mod["Qinv"], mod["Rinv"], mod["z"])
     _close(A_diag, rd)
+
+
+@pytest.mark.parametrize("N,n,m", [(3, 16, 64), (4, 70, 130)])
+def test_assembly_with_diagonal_R_matches_oracle(N, n, m):
+    from paper_2509_03015_gb300 import kalman_assemble
+    mod = inputs.kalman_model(N, n, m, seed=5 * N + m)
+    mod["Rinv"] = np.ascontiguousarray(np.stack([np.diag(R) for R in mod["Rinv"]]))
+    d = _dev(mod)
+    A_diag, A_sub, B = kalman_assemble(d["G"], d["H"], d["Qinv"], d["Rinv"], d["z"], d["zeta"])
+    rd, rs, rb = oracle.kalman_assemble(mod["G"], mod["H"], mod["Qinv"], mod["Rinv"], mod["z"], mod["zeta"])
+    _close(A_diag, rd)
+    _close(A_sub, rs)
+    _close(B, rb)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+def test_neuro_shaped_instance_solves(precision):
+    from paper_2509_03015_gb300 import Solver, kalman_assemble
+    N, n, m = 20, 32, 128
+    mod = inputs.kalman_neuro_model(N, n, m, seed=2)
+    d = _dev(mod)
+    A_diag, A_sub, B = kalman_assemble(d["G"], d["H"], d["Qinv"], d["Rinv"], d["z"], d["zeta"])
+    rd, rs, rb = oracle.kalman_assemble(mod["G"], mod["H"], mod["Qinv"], mod["Rinv"], mod["z"], mod["zeta"])
+    _close(A_diag, rd)
+    _close(B, rb)
+    sol = Solver(N, n, d_max=1, precision=precision)
+    X = sol.factor_solve(A_diag, A_sub, B)
+    sol.close()
+    Xr = oracle.solve_system(rd, rs, rb)
+    np.testing.assert_allclose(X.cpu().numpy(), Xr, rtol=0, atol=1e-9 * max(1.0, np.abs(Xr).max()))

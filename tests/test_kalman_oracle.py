@@ -31,12 +31,17 @@ def _model(N, n, m, seed):
     return G, H, Qinv, Rinv, z, zeta
 
 
+@pytest.mark.parametrize("diag_r", [False, True])
 @pytest.mark.parametrize("N,n,m", [(1, 3, 2), (2, 2, 3), (5, 4, 3), (6, 3, 5)])
-def test_assembly_equals_dense_normal_equations(N, n, m):
+def test_assembly_equals_dense_normal_equations(N, n, m, diag_r):
     # minimise 1/2 |Hx - z|^2_{R^-1} + 1/2 |Gx - zeta|^2_{Q^-1}: the stacked state
     # operator has I on its block diagonal and -G_k below it; the normal
     # equations are (H^T R^-1 H + G^T Q^-1 G) x = H^T R^-1 z + G^T Q^-1 zeta
     G, H, Qinv, Rinv, z, zeta = _model(N, n, m, seed=N * 10 + n)
+    r_in = Rinv
+    if diag_r:
+        r_in = np.stack([np.diag(R) for R in Rinv])  # keep only the diagonals
+        Rinv = np.stack([np.diag(r) for r in r_in])
     Gbig = np.eye(N * n)
     for k in range(1, N):
         Gbig[k * n:(k + 1) * n, (k - 1) * n:k * n] = -G[k]
@@ -49,7 +54,7 @@ def test_assembly_equals_dense_normal_equations(N, n, m):
         Rbig[k * m:(k + 1) * m, k * m:(k + 1) * m] = Rinv[k]
     A = Hbig.T @ Rbig @ Hbig + Gbig.T @ Qbig @ Gbig
     b = Hbig.T @ Rbig @ z.reshape(-1) + Gbig.T @ Qbig @ zeta.reshape(-1)
-    A_diag, A_sub, B = oracle.kalman_assemble(G, H, Qinv, Rinv, z, zeta)
+    A_diag, A_sub, B = oracle.kalman_assemble(G, H, Qinv, r_in, z, zeta)
     Ad = _dense(A_diag, A_sub)
     np.testing.assert_allclose(Ad, A, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(B.reshape(-1), b, rtol=1e-12, atol=1e-12)
