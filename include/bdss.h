@@ -81,7 +81,8 @@ typedef enum {
 typedef struct {
   int64_t level;        /* NOT_SPD: reduction level of the failing pivot (-1: none) */
   int64_t block;        /* NOT_SPD: original 0-based block index of that pivot */
-  int32_t iters;        /* mixed precision: refinement steps taken (0 in FP64) */
+  int32_t iters;        /* mixed precision: refinement steps taken, plain corrections
+                           plus CG iterations (0 in FP64) */
   int32_t reserved;
   double backward_err;  /* mixed precision: ||B-AX||_inf / (||A||_inf ||X||_inf) of
                            the returned X, FP64 residual; -1 when not computed */
@@ -102,9 +103,20 @@ typedef enum {
   BDSS_OPT_DEBUG_GUARDS = 5,    /* 1: after every call, check the guard band (256 bytes
                                    of a fixed pattern) after each workspace buffer;
                                    an overwritten band gives BDSS_ERR_GUARD */
-  BDSS_OPT_DEBUG_CORRUPT_GUARD = 6 /* test hook: overwrite, from the host, one byte of
+  BDSS_OPT_DEBUG_CORRUPT_GUARD = 6, /* test hook: overwrite, from the host, one byte of
                                    the guard band of workspace buffer `value` (1-based,
                                    allocation order) to exercise the check */
+  BDSS_OPT_REFINE_KRYLOV = 7,   /* mixed precision: 0 = plain refinement only;
+                                   1 (default) = when plain refinement stalls (kappa(A)
+                                   near or above 1/u_32 ~ 1e7) or has used its
+                                   BDSS_OPT_MAX_REFINE steps, cycles of FP64 conjugate
+                                   gradients preconditioned by the FP32 factors;
+                                   2 = those cycles from the first correction on.
+                                   BDSS_OPT_MAX_REFINE = 0 allows no correction at all.
+                                   The CG vectors (4 N n d_max doubles) are allocated on
+                                   first use; at most 4 cycles, each restarted from the
+                                   true FP64 residual */
+  BDSS_OPT_MAX_KRYLOV_ITERS = 8 /* mixed precision: CG iterations per cycle (default 300) */
 } bdss_option;
 
 /*
@@ -204,10 +216,16 @@ bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, int32_t rinv_d
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);
 
 /* Test hook: the k-th device or page-locked allocation of every following
- * bdss_create or bdss_kalman_assemble (counted per call, 1-based) fails as if
- * the memory were exhausted; 0 turns it off.  The call must then return
- * BDSS_ERR_ALLOC having freed what it had allocated. */
+ * bdss_create, bdss_kalman_assemble or first CG refinement of a handle
+ * (counted per call, 1-based) fails as if the memory were exhausted; 0 turns
+ * it off.  The call must then return BDSS_ERR_ALLOC; bdss_create frees what
+ * it had allocated, a solve keeps its buffers for bdss_destroy. */
 bdss_status bdss_debug_fail_alloc(int32_t k);
+
+/* Refinement steps of the handle's last mixed-precision solve (host pointers,
+ * either may be NULL): plain corrections X += M^-1 r and preconditioned-CG
+ * iterations (see BDSS_OPT_REFINE_KRYLOV).  bdss_info.iters is their sum. */
+bdss_status bdss_last_refine_stats(bdss_handle h, int32_t *plain_steps, int32_t *cg_iters);
 
 /* Launch configuration the handle chose at creation (host pointers, any may
  * be NULL): resident CTAs per SM of its persistent kernel (from the

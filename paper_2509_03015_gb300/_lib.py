@@ -17,7 +17,7 @@ STATUS_NAMES = {
 }
 PRECISIONS = {"fp64": 0, "fp32_ir": 1, "tf32_ir": 2}
 OPTIONS = {"timeout_ms": 0, "persistent": 1, "max_refine": 2, "target_berr_e18": 3, "debug_skip_arrive": 4,
-           "debug_guards": 5, "debug_corrupt_guard": 6}
+           "debug_guards": 5, "debug_corrupt_guard": 6, "refine_krylov": 7, "max_krylov_iters": 8}
 
 
 class bdss_info(ctypes.Structure):
@@ -38,6 +38,7 @@ SIGNATURES = {
     "bdss_logdet": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "bdss_last_launch_stats": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bdss_last_trace": (_i32, [_vp, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32)]),
+    "bdss_last_refine_stats": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "bdss_get_launch_config": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "bdss_debug_fail_alloc": (_i32, [_i32]),
     "bdss_destroy": (_i32, [_vp]),

@@ -15,6 +15,7 @@
 #include "../../include/bdss.h"
 #include "bdss_launch.h"
 #include "bdss_kalman.h"
+#include "bdss_krylov.h"
 
 using namespace bdss;
 
@@ -53,6 +54,13 @@ struct bdss_ctx {
   int persistent = 1;
   int max_refine = 10;
   double target = 1e-14;
+  int krylov = 1;        // 0: plain refinement only; 1: CG when it stalls; 2: CG from the start
+  int max_krylov = 300;  // CG iterations per cycle
+  // mixed: preconditioned-CG refinement vectors (N n d_max each) and scalars,
+  // allocated on first use
+  double *kr_R = nullptr, *kr_Z = nullptr, *kr_P = nullptr, *kr_Q = nullptr;
+  double *kr_part = nullptr, *kr_sc = nullptr;
+  int last_plain = 0, last_cg = 0;  // refinement steps of the last solve
   int skip_barrier = 0;
   // stats of the last call
   int64_t launches = 0;
@@ -291,6 +299,12 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->Y32);
   cudaFree(h->R32);
   cudaFree(h->partial);
+  cudaFree(h->kr_R);
+  cudaFree(h->kr_Z);
+  cudaFree(h->kr_P);
+  cudaFree(h->kr_Q);
+  cudaFree(h->kr_part);
+  cudaFree(h->kr_sc);
   cudaFree(h->dst);
   if (h->hst) cudaFreeHost(h->hst);
   delete h;
@@ -397,6 +411,14 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
     case BDSS_OPT_DEBUG_GUARDS:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
       h->debug_guards = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_REFINE_KRYLOV:
+      if (value < 0 || value > 2) return BDSS_ERR_INVALID_ARG;
+      h->krylov = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_MAX_KRYLOV_ITERS:
+      if (value < 1 || value > 100000) return BDSS_ERR_INVALID_ARG;
+      h->max_krylov = (int)value;
       return BDSS_OK;
     case BDSS_OPT_DEBUG_CORRUPT_GUARD: {
       // test hook: overwrite one byte of buffer `value`'s guard band from the host
@@ -510,54 +532,163 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
 }
 
 // Mixed precision: X already holds the FP32 solve; refine with FP64 residuals.
-static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_info *info) {
-  double prev = INFINITY;
-  int iters = 0;
-  bdss_status result = BDSS_ERR_NO_CONVERGENCE;
-  double berr = -1.0;
-  for (int it = 0;; ++it) {
-    cudaError_t e = reset_status(h);
-    const int with_norm = h->norm_valid ? 0 : 1;
-    if (e == cudaSuccess)
-      e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
-                                          (int)std::min<long long>(h->N, 2LL * h->sms), h->stream)
-                   : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
-                                     grid_for(h, h->N) * 2, h->stream);
-    h->launches += 1;
+// Backward error ||B - A X||_inf / (||A||_inf ||X||_inf) of the current X from
+// the FP64 residual kernel, which also leaves the residual in R32 (FP32) for a
+// plain correction and forms ||A||_inf on its first call.
+static bdss_status residual_berr(bdss_ctx *h, const double *B, const double *X, int d, double *berr) {
+  cudaError_t e = reset_status(h);
+  const int with_norm = h->norm_valid ? 0 : 1;
+  if (e == cudaSuccess)
+    e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
+                                        (int)std::min<long long>(h->N, 2LL * h->sms), h->stream)
+                 : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
+                                   grid_for(h, h->N) * 2, h->stream);
+  h->launches += 1;
+  if (e != cudaSuccess) return cuda_fail(e);
+  bdss_status st = finish(h, nullptr);
+  if (st != BDSS_OK) return st;
+  if (with_norm) {
+    uint64_t bits = h->hst->nrm[2];
+    memcpy(&h->normA, &bits, sizeof(double));
+    h->norm_valid = true;
+  }
+  double rn, xn;
+  uint64_t b0 = h->hst->nrm[0], b1 = h->hst->nrm[1];
+  memcpy(&rn, &b0, sizeof(double));
+  memcpy(&xn, &b1, sizeof(double));
+  const double den = h->normA * xn;
+  *berr = den > 0 ? rn / den : (rn == 0 ? 0.0 : INFINITY);
+  return BDSS_OK;
+}
+
+// The CG vectors and scalars, allocated on the first CG refinement of the
+// handle (allocations counted per call for the allocation-failure hook).
+static bdss_status krylov_alloc(bdss_ctx *h) {
+  const size_t vec = (size_t)h->N * h->n * h->d_max * sizeof(double);
+  t_alloc_count = 0;
+  double **bufs[4] = {&h->kr_R, &h->kr_Z, &h->kr_P, &h->kr_Q};
+  for (double **b : bufs)
+    if (!*b && !ws_alloc(h, (void **)b, vec)) return BDSS_ERR_ALLOC;
+  if (!h->kr_part && !ws_alloc(h, (void **)&h->kr_part, kPartWords * sizeof(double))) return BDSS_ERR_ALLOC;
+  if (!h->kr_sc && !ws_alloc(h, (void **)&h->kr_sc, kScWords * sizeof(double))) return BDSS_ERR_ALLOC;
+  return BDSS_OK;
+}
+
+// z = M^-1 r: the FP32 substitutions on the stored factors, FP64 in and out.
+static bdss_status apply_precond(bdss_ctx *h, int d) {
+  cudaError_t e = reset_status(h);
+  Args<float> a = base_args<float>(h);
+  a.d = d;
+  a.B64 = h->kr_R;
+  a.Y = h->Y32;
+  a.X64 = h->kr_Z;
+  a.x_accumulate = 0;
+  if (e == cudaSuccess) e = run_levels<float>(h, a, false, true);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return finish(h, nullptr);
+}
+
+// One cycle of preconditioned CG on A dX = B - A X from the current X, which
+// is updated in place.  Stops when the recursively updated residual meets half
+// the target backward error, when it has not halved its best value for
+// kCgStall iterations, or after max_krylov iterations.
+static bdss_status krylov_cycle(bdss_ctx *h, const double *B, double *X, int d) {
+  constexpr int kCgStall = 50;
+  const long long rows = h->N * h->n;
+  const int gD = col_dots_grid(rows, d), gU = pcg_update_grid(rows);
+  cudaStream_t s = h->stream;
+  double *R = h->kr_R, *Z = h->kr_Z, *P = h->kr_P, *Q = h->kr_Q, *part = h->kr_part, *sc = h->kr_sc;
+  cudaError_t e = launch_btd_apply(h->N, h->n, d, h->A_diag, h->A_sub, X, B, R, h->sms, s);  // r = B - A X
+  h->launches += 1;
+  if (e != cudaSuccess) return cuda_fail(e);
+  bdss_status st = apply_precond(h, d);
+  if (st != BDSS_OK) return st;
+  e = launch_col_dots(rows, d, Z, R, nullptr, nullptr, part, gD, s);
+  if (e == cudaSuccess) e = launch_pcg_scalars(gD, d, part, kPcgStart, sc, s);
+  if (e == cudaSuccess) e = launch_pcg_direction(rows, d, sc, Z, P, 1, h->sms, s);
+  h->launches += 3;
+  if (e != cudaSuccess) return cuda_fail(e);
+  double best = INFINITY;
+  int since_best = 0;
+  for (int k = 0; k < h->max_krylov; ++k) {
+    e = launch_btd_apply(h->N, h->n, d, h->A_diag, h->A_sub, P, nullptr, Q, h->sms, s);  // q = A p
+    if (e == cudaSuccess) e = launch_col_dots(rows, d, P, Q, nullptr, nullptr, part, gD, s);
+    if (e == cudaSuccess) e = launch_pcg_scalars(gD, d, part, kPcgAlpha, sc, s);
+    if (e == cudaSuccess) e = launch_pcg_update(rows, d, sc, P, Q, X, R, part, gU, s);
+    if (e == cudaSuccess) e = launch_pcg_scalars(gU, d, part, kPcgNorms, sc, s);
+    double nrm[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nrm, sc + kScNorm, sizeof(nrm), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    h->launches += 5;
     if (e != cudaSuccess) return cuda_fail(e);
-    bdss_status st = finish(h, nullptr);
-    if (st != BDSS_OK) return st;
-    if (with_norm) {
-      uint64_t bits = h->hst->nrm[2];
-      memcpy(&h->normA, &bits, sizeof(double));
-      h->norm_valid = true;
+    ++h->last_cg;
+    const double den = h->normA * nrm[1];
+    const double est = den > 0 ? nrm[0] / den : (nrm[0] == 0 ? 0.0 : INFINITY);
+    if (!(est < INFINITY) || est <= 0.5 * h->target) break;
+    if (est < 0.5 * best) {
+      best = est;
+      since_best = 0;
+    } else if (++since_best >= kCgStall) {
+      break;
     }
-    double rn, xn;
-    uint64_t b0 = h->hst->nrm[0], b1 = h->hst->nrm[1];
-    memcpy(&rn, &b0, sizeof(double));
-    memcpy(&xn, &b1, sizeof(double));
-    const double den = h->normA * xn;
-    berr = den > 0 ? rn / den : (rn == 0 ? 0.0 : INFINITY);
-    if (berr <= h->target) { result = BDSS_OK; break; }
-    if (it > 0 && !(berr < 0.5 * prev)) break;   // stagnation
-    if (it >= h->max_refine) break;
-    prev = berr;
-    // correction: solve A dX = r in FP32, X += dX (FP64), fused in the downward pass
-    e = reset_status(h);
-    Args<float> a = base_args<float>(h);
-    a.d = d;
-    a.Bt = h->R32;
-    a.Y = h->Y32;
-    a.X64 = X;
-    a.x_accumulate = 1;
-    if (e == cudaSuccess) e = run_levels<float>(h, a, false, true);
-    if (e != cudaSuccess) return cuda_fail(e);
-    st = finish(h, nullptr);
+    st = apply_precond(h, d);  // z = M^-1 r
     if (st != BDSS_OK) return st;
-    ++iters;
+    e = launch_col_dots(rows, d, Z, R, Z, Q, part, gD, s);
+    if (e == cudaSuccess) e = launch_pcg_scalars(gD, d, part, kPcgBeta, sc, s);
+    if (e == cudaSuccess) e = launch_pcg_direction(rows, d, sc, Z, P, 0, h->sms, s);
+    h->launches += 3;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return BDSS_OK;
+}
+
+// Mixed precision: refine X (the FP32 solution, stored in FP64) until its
+// backward error meets the target.  Plain refinement first (X += M^-1 r with
+// the FP32 residual, at most max_refine steps); when that stalls -- kappa(A)
+// u_32 near or above one -- or runs out of steps, or from the start (option),
+// cycles of FP64 CG preconditioned by M.  max_refine = 0 means no correction
+// of either kind.
+static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_info *info) {
+  constexpr int kMaxCgCycles = 4;
+  double prev = INFINITY, berr = -1.0;
+  int cycles = 0;
+  bdss_status result = BDSS_ERR_NO_CONVERGENCE;
+  h->last_plain = 0;
+  h->last_cg = 0;
+  for (int it = 0;; ++it) {
+    bdss_status st = residual_berr(h, B, X, d, &berr);
+    if (st != BDSS_OK) return st;
+    if (berr <= h->target) { result = BDSS_OK; break; }
+    const bool stalled = it > 0 && !(berr < 0.5 * prev);
+    const bool plain_done = stalled || it >= h->max_refine;
+    const bool cg = cycles > 0 || h->krylov == 2 || (h->krylov == 1 && plain_done);
+    if (!cg) {
+      if (plain_done) break;
+      prev = berr;
+      // correction: solve A dX = r in FP32, X += dX (FP64), fused in the downward pass
+      cudaError_t e = reset_status(h);
+      Args<float> a = base_args<float>(h);
+      a.d = d;
+      a.Bt = h->R32;
+      a.Y = h->Y32;
+      a.X64 = X;
+      a.x_accumulate = 1;
+      if (e == cudaSuccess) e = run_levels<float>(h, a, false, true);
+      if (e != cudaSuccess) return cuda_fail(e);
+      st = finish(h, nullptr);
+      if (st != BDSS_OK) return st;
+      ++h->last_plain;
+      continue;
+    }
+    if (h->max_refine == 0 || cycles >= kMaxCgCycles || (cycles > 0 && stalled)) break;
+    prev = berr;
+    st = krylov_alloc(h);
+    if (st == BDSS_OK) st = krylov_cycle(h, B, X, d);
+    if (st != BDSS_OK) return st;
+    ++cycles;
   }
   if (info) {
-    info->iters = iters;
+    info->iters = h->last_plain + h->last_cg;
     info->backward_err = berr;
   }
   return result;
@@ -705,6 +836,13 @@ bdss_status bdss_tc_selftest(double *max_rel_err) {
 bdss_status bdss_debug_fail_alloc(int32_t k) {
   if (k < 0) return BDSS_ERR_INVALID_ARG;
   g_fail_alloc.store(k);
+  return BDSS_OK;
+}
+
+bdss_status bdss_last_refine_stats(bdss_handle h, int32_t *plain_steps, int32_t *cg_iters) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  if (plain_steps) *plain_steps = h->last_plain;
+  if (cg_iters) *cg_iters = h->last_cg;
   return BDSS_OK;
 }
 

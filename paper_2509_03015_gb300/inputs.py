@@ -19,6 +19,8 @@ Generators:
                     the parity tests so that an indexing mistake cannot hide
                     behind repeated blocks.
   tridiag_121    -- n = 1, A = tridiag(-1, 2, -1), B = 1.
+  laplace_btd    -- block 1-D Laplacian with PSD block perturbations sharing a
+                    null vector: kappa(A) ~ N^2, beyond plain FP32 refinement.
   kalman_model   -- a time-varying state-space model (G_k, H_k, Q_k^-1, R_k^-1,
                     z_k, zeta_k), the input of the on-device assembly of the
                     Kalman-smoother normal equations.
@@ -205,6 +207,27 @@ def random_btd(N: int, n: int, d: int, seed: int, coupling: float = 1.0):
         A_diag[i] = M @ M.T / n + s * np.eye(n) + (skew - skew.T)
     B = rng.standard_normal((N, n, d))
     return dict(A_diag=A_diag, A_sub=A_sub, B=B)
+
+
+def laplace_btd(N: int, n: int, d: int, seed: int):
+    """Ill-conditioned SPD system: a 1-D Laplacian coupling of blocks,
+    A_{i+1,i} = -I, A_ii = 2 I + S_i with S_i = P M_i M_i^T P / (2n) and
+    P = I - v v^T for one random unit vector v, so every S_i is PSD with v in
+    its null space.  On span{v} (x) R^N the matrix is tridiag(-1, 2, -1)
+    exactly, with smallest eigenvalue 4 sin^2(pi / (2 (N + 1))), and
+    kappa(A) ~ 0.6 N^2 (about 6e8 at N = 32768).  Drawn from
+    numpy.random.default_rng(seed) in the order v, M (N, n, n), B (N n, d)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(n)
+    v /= np.linalg.norm(v)
+    Pv = np.eye(n) - np.outer(v, v)
+    M = rng.standard_normal((N, n, n))
+    PM = np.matmul(Pv, M)
+    A_diag = 2.0 * np.eye(n) + np.matmul(PM, PM.transpose(0, 2, 1)) / (2 * n)
+    A_sub = np.empty((max(N - 1, 0), n, n))
+    A_sub[:] = -np.eye(n)
+    B = rng.standard_normal((N * n, d)).reshape(N, n, d)
+    return dict(A_diag=A_diag, A_sub=A_sub, B=np.ascontiguousarray(B))
 
 
 def tridiag_121(N: int, d: int = 1):

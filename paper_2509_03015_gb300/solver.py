@@ -118,6 +118,14 @@ class Solver:
         _lib.check(self.lib.bdss_last_launch_stats(self.h, ctypes.byref(k), ctypes.byref(b)), "bdss_last_launch_stats")
         return k.value, b.value
 
+    def refine_stats(self):
+        """(plain corrections, preconditioned-CG iterations) of the last
+        mixed-precision solve."""
+        p, c = ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(self.lib.bdss_last_refine_stats(self.h, ctypes.byref(p), ctypes.byref(c)),
+                   "bdss_last_refine_stats")
+        return p.value, c.value
+
     def launch_config(self):
         """(resident CTAs per SM, SM count, dynamic shared memory bytes per
         CTA) of this handle's persistent kernel."""
