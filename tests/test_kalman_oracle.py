@@ -84,3 +84,23 @@ def test_assembled_system_is_spd_and_solves():
     np.linalg.cholesky(A)  # SPD
     X = oracle.solve_system(A_diag, A_sub, B)
     np.testing.assert_allclose(A @ X.reshape(-1), B.reshape(-1), rtol=1e-10, atol=1e-10)
+
+
+def test_neuro_shaped_model_follows_its_recipe():
+    # damped 2-D rotations (|eigenvalues| = rho in [0.95, 0.999]), G_0 = I,
+    # dense SPD Q^-1, tall well-conditioned H, diagonal R^-1 = 1, zeta only at 0
+    N, n, m = 5, 16, 64
+    mod = inputs.kalman_neuro_model(N, n, m, seed=7)
+    G, H, Qinv, Rinv, zeta = mod["G"], mod["H"], mod["Qinv"], mod["Rinv"], mod["zeta"]
+    np.testing.assert_array_equal(G[0], np.eye(n))
+    ev = np.abs(np.linalg.eigvals(G[1]))
+    assert ev.min() >= 0.95 - 1e-12 and ev.max() <= 0.999 + 1e-12
+    GtG = G[1].T @ G[1]
+    np.testing.assert_allclose(GtG, np.diag(np.diag(GtG)), atol=1e-14)  # scaled orthogonal blocks
+    assert np.linalg.eigvalsh(Qinv[0]).min() > 0 and np.count_nonzero(Qinv[0]) == n * n
+    sv = np.linalg.svd(H[0], compute_uv=False)
+    assert sv.max() / sv.min() < 10
+    assert Rinv.shape == (N, m) and np.all(Rinv == 1.0)
+    assert np.any(zeta[0] != 0) and not np.any(zeta[1:])
+    A_diag, A_sub, _ = oracle.kalman_assemble(G, H, Qinv, Rinv, mod["z"], zeta)
+    np.linalg.cholesky(_dense(A_diag, A_sub))
