@@ -20,7 +20,8 @@ def test_laplace_btd_smallest_eigenvalue_is_the_laplacian_one(N, n):
 
 
 def test_refine_options_and_stats_reject_bad_arguments():
-    from paper_2509_03015_gb300 import _lib
+    from paper_2509_03015_gb300 import _lib, build
+    build.build()
     lib = _lib.load()
     assert lib.bdss_set_option(None, 7, 1) == 1
     assert lib.bdss_set_option(None, 8, 10) == 1
