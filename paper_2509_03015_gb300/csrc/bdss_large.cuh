@@ -26,7 +26,7 @@ constexpr int kTilePad = kTile + 1;
 
 __host__ __device__ inline int ntiles(int n) { return (n + kTile - 1) / kTile; }
 // Vectors per forward-substitution task: one 64-wide gemm tile of them.
-__host__ __device__ inline int vec_tile(int elem_size) { return 64; }
+__host__ __device__ inline int vec_tile(int /*elem_size: the same for FP32 and FP64*/) { return 64; }
 
 // Strided matrix view: element (r, c) at p[r * rs + c * cs]; zero outside
 // rows x cols.  Global views load through L2 (written by other CTAs across
