@@ -333,3 +333,77 @@ def test_tally_matches_counted_ops(oracle_mod, N, n, d):
     fac, sol = _counted_thomas(N, n, d)
     assert abs(t["factor"] - fac) < 1e-9 * max(fac, 1)
     assert abs(t["solve"] - sol) < 1e-9 * max(sol, 1)
+
+
+# ---- ||A||_inf: the denominator of every backward-error check ------------------
+
+def _norm_cases():
+    rng = np.random.default_rng(7)
+    cases = []
+    for N, n in [(1, 1), (1, 5), (2, 3), (7, 4), (16, 6)]:
+        s = inputs.random_btd(N, n, 1, seed=11 * N + n)
+        cases.append((f"random-N{N}-n{n}", s["A_diag"], s["A_sub"]))
+    # A_diag with a large skew part: sym(.) must halve it away, so dropping
+    # the 1/2 or reading one triangle only changes the row sums
+    s = inputs.random_btd(5, 4, 1, seed=99)
+    skew = 3.0 * rng.standard_normal((5, 4, 4))
+    cases.append(("skewed", s["A_diag"] + skew - skew.transpose(0, 2, 1), s["A_sub"]))
+    # one dominant sub-diagonal block, so the max row is decided by whether
+    # A_{i+1,i} or its transpose is added to row block i
+    s = inputs.random_btd(4, 3, 1, seed=5)
+    A_sub = s["A_sub"].copy()
+    A_sub[1] = 0.0
+    A_sub[1][0, :] = [40.0, -1.0, 2.0]
+    cases.append(("dominant-sub", s["A_diag"], A_sub))
+    k = inputs.kalman_btd(6, 8, 4, 1, 0.95, 0)
+    cases.append(("kalman", k["A_diag"], k["A_sub"]))
+    return cases
+
+
+@pytest.mark.parametrize("case", _norm_cases(), ids=lambda c: c[0])
+def test_norm_inf_A_matches_dense(oracle_mod, case):
+    """||A||_inf of the operator of Eq. 1 (max absolute row sum over sym(A_ii),
+    A_{i+1,i} below and A_{i+1,i}^T above) equals numpy's norm of the dense
+    matrix: a sum of at most 3n nonnegative terms, so the two agree to a few
+    ulps."""
+    _, A_diag, A_sub = case
+    ref = np.linalg.norm(dense_A(A_diag, A_sub), np.inf)
+    got = oracle_mod.norm_inf_A(A_diag, A_sub)
+    n = A_diag.shape[1]
+    assert abs(got - ref) <= 3 * n * 2.3e-16 * ref
+
+
+@pytest.mark.parametrize("N,expect", [(1, 2.0), (2, 3.0), (3, 4.0), (50, 4.0)])
+def test_norm_inf_A_tridiag_closed_form(oracle_mod, N, expect):
+    """tridiag(-1, 2, -1): row sums 2 (N = 1), 3 at the two ends, 4 inside."""
+    s = inputs.tridiag_121(N)
+    assert oracle_mod.norm_inf_A(s["A_diag"], s["A_sub"]) == expect
+
+
+# ---- the batched CPU baseline is the per-instance solve -------------------------
+
+def test_factor_solve_batched_matches_per_instance(oracle_mod):
+    """A ragged batch (N = 1 included, mixed n): every instance's X equals the
+    single-system oracle bitwise, so no instance reads another's pointers;
+    two tiny instances are also checked against a dense LAPACK solve."""
+    shapes = [(1, 3), (2, 1), (5, 4), (1, 1), (9, 2), (17, 6), (3, 5), (33, 3)]
+    d = 2
+    systems = [inputs.random_btd(N, n, d, seed=300 + k) for k, (N, n) in enumerate(shapes)]
+    Xs, threads = oracle_mod.factor_solve_batched(systems)
+    assert threads >= 1 and len(Xs) == len(systems)
+    for s, X in zip(systems, Xs):
+        ref = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
+        assert X.shape == s["B"].shape
+        assert np.array_equal(X, ref)
+    for k in (2, 6):
+        s = systems[k]
+        Xd = np.linalg.solve(dense_A(s["A_diag"], s["A_sub"]), dense_B(s["B"]))
+        np.testing.assert_allclose(dense_B(Xs[k]), Xd, rtol=1e-12, atol=1e-12)
+
+
+def test_factor_solve_batched_reports_failing_instance(oracle_mod):
+    systems = [inputs.random_btd(N, 3, 1, seed=N) for N in (4, 6, 2)]
+    systems[1]["A_diag"][3] -= 40.0 * np.eye(3)
+    with pytest.raises(oracle_mod.NotSPDError) as e:
+        oracle_mod.factor_solve_batched(systems)
+    assert e.value.block == (1, 3)
