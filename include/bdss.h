@@ -116,8 +116,24 @@ typedef enum {
                                    The CG vectors (4 N n d_max doubles) are allocated on
                                    first use; at most 4 cycles, each restarted from the
                                    true FP64 residual */
-  BDSS_OPT_MAX_KRYLOV_ITERS = 8 /* mixed precision: CG iterations per cycle (default 300) */
+  BDSS_OPT_MAX_KRYLOV_ITERS = 8, /* mixed precision: CG iterations per cycle (default 300) */
+  BDSS_OPT_KERNEL_TIMING = 9    /* 1: time every launch (group) of each following call with
+                                   CUDA events recorded on the handle's stream, by kernel
+                                   class (bdss_kernel_class); read with
+                                   bdss_last_kernel_times.  0 (default): off.  The first
+                                   switch-on creates 512 events. */
 } bdss_option;
+
+/* Kernel classes of bdss_last_kernel_times. */
+typedef enum {
+  BDSS_KT_FACTOR = 0,      /* factorisation passes (with the first solve when fused) on CUDA cores */
+  BDSS_KT_SCHUR_TC = 1,    /* BDSS_TF32_IR, n > 64: the tensor-core Schur-update launches of a factorisation */
+  BDSS_KT_SOLVE = 2,       /* the solve pass of bdss_solve on stored factors */
+  BDSS_KT_CORRECTION = 3,  /* mixed precision: refinement corrections X += M^-1 (B - A X) */
+  BDSS_KT_RESIDUAL = 4,    /* mixed precision: FP64 residuals B - A X (with the backward-error norms) */
+  BDSS_KT_KRYLOV = 5,      /* mixed precision: CG refinement kernels and their preconditioner solves */
+  BDSS_KT_CLASSES = 6
+} bdss_kernel_class;
 
 /*
  * Create a solver for systems with N >= 1 blocks of size 1 <= n <= 256 and
@@ -250,6 +266,16 @@ bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity
  * (host pointer).  Allocates and frees its own small buffers. */
 bdss_status bdss_tc_selftest(double *max_rel_err);
 
+/* Device time of the handle's last bdss_factor, bdss_solve or
+ * bdss_factor_solve by kernel class, with BDSS_OPT_KERNEL_TIMING on: ms[c]
+ * (milliseconds between the CUDA events recorded on the handle's stream
+ * before and after each launch or launch group of class c, summed) and
+ * launches[c] (kernel launches in those groups; may be NULL), for
+ * c < min(classes, BDSS_KT_CLASSES).  Zeros when timing is off.  Host
+ * pointers.  The paper reports per-phase wall-clock times (factor, solve);
+ * this is the same split per kernel, on the device. */
+bdss_status bdss_last_kernel_times(bdss_handle h, double *ms, int64_t *launches, int32_t classes);
+
 /* Description of the last CUDA runtime error that made a bdss_* call on this
  * host thread return BDSS_ERR_CUDA ("no error" if none).  Never NULL. */
 const char *bdss_last_cuda_error(void);
@@ -309,12 +335,18 @@ bdss_status bdss_factor_solve_batched(int32_t K, const int64_t *N_k, const int32
  * the library holds from load until process exit.
  *
  * Arguments are those of bdss_create + bdss_factor_solve for one FP64 system
- * (same layouts; X may equal B); the call returns after synchronising
- * `cuda_stream`.  Systems whose workspace (about 3 N n^2 doubles) does not fit
- * the array are rejected with BDSS_ERR_UNSUPPORTED before anything is
- * launched.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) and sets kernel attributes; make that first
- * call before any stream capture.  All calls on a device share the one array
+ * of blocks n <= 64 (same layouts; X may equal B; inputs in device memory or
+ * memory the device can read in place); the result equals that of the
+ * allocating entry point, with the same launch configuration.  The call
+ * synchronises `cuda_stream` before it returns, to read the status word.
+ * Returned before anything is launched: BDSS_ERR_INVALID_ARG for a bad size
+ * or pointer, BDSS_ERR_UNSUPPORTED for n > 64 (the tiled path of larger
+ * blocks is not offered here), for a shared-memory need beyond the device's
+ * limit, and for systems whose workspace (about 3 N n^2 doubles) does not fit
+ * the array.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress), the device's limits, and raises the kernels'
+ * shared-memory limits; make that first call before any stream capture.
+ * Later calls make no attribute calls.  All calls on a device share the one array
  * and it keeps the last call's contents (the status word is cleared at the
  * start of each call): calls that overlap on the GPU -- on different streams
  * or host threads -- race and must be serialised by the caller.

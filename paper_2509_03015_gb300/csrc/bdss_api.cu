@@ -67,6 +67,16 @@ struct bdss_ctx {
   int64_t barriers = 0;
   int trace_count = 0;               // barrier stamps of the last persistent launch
   long long trace[kTraceSlots] = {};
+  // per-kernel-class device times (BDSS_OPT_KERNEL_TIMING): pairs of events
+  // recorded on the handle's stream around launches, harvested after the
+  // stream is synchronised
+  int ktiming = 0;
+  int kt_cls = BDSS_KT_FACTOR;       // class of the launches being issued
+  std::vector<cudaEvent_t> kt_ev;    // event pool (pairs)
+  std::vector<int> kt_pair_cls, kt_pair_n;
+  int kt_used = 0;                   // pairs recorded since the last harvest
+  double kt_ms[BDSS_KT_CLASSES] = {};
+  int64_t kt_n[BDSS_KT_CLASSES] = {};
   // guard bands after every workspace buffer (checked with the debug option)
   struct Guard { void *base; size_t bytes; };
   std::vector<Guard> guards;
@@ -123,6 +133,50 @@ static bdss_status cuda_fail(cudaError_t e) {
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// ---- per-kernel-class timing ------------------------------------------------
+static constexpr int kKtPairs = 256;
+
+// Add the elapsed times of the recorded pairs to their classes (the events
+// have completed once the stream is synchronised; the wait on the last one
+// covers a harvest forced by a full pool).
+static void kt_harvest(bdss_ctx *h) {
+  if (h->kt_used == 0) return;
+  cudaEventSynchronize(h->kt_ev[2 * (h->kt_used - 1) + 1]);
+  for (int i = 0; i < h->kt_used; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->kt_ev[2 * i], h->kt_ev[2 * i + 1]) == cudaSuccess) {
+      h->kt_ms[h->kt_pair_cls[i]] += ms;
+      h->kt_n[h->kt_pair_cls[i]] += h->kt_pair_n[i];
+    }
+  }
+  cudaGetLastError();
+  h->kt_used = 0;
+}
+
+static void kt_reset(bdss_ctx *h) {
+  h->kt_used = 0;
+  for (int c = 0; c < BDSS_KT_CLASSES; ++c) {
+    h->kt_ms[c] = 0.0;
+    h->kt_n[c] = 0;
+  }
+}
+
+// Open a timed group of launches of class `cls` (no-op unless timing is on).
+static void kt_begin(bdss_ctx *h, int cls) {
+  if (!h->ktiming) return;
+  if (h->kt_used == kKtPairs) kt_harvest(h);
+  h->kt_pair_cls[h->kt_used] = cls;
+  cudaEventRecord(h->kt_ev[2 * h->kt_used], h->stream);
+}
+
+// Close the group opened by kt_begin; it held `launches` kernel launches.
+static void kt_end(bdss_ctx *h, int launches) {
+  if (!h->ktiming) return;
+  cudaEventRecord(h->kt_ev[2 * h->kt_used + 1], h->stream);
+  h->kt_pair_n[h->kt_used] = launches;
+  ++h->kt_used;
+}
+
 static bool is_mixed(const bdss_ctx *h) { return h->prec != BDSS_FP64; }
 
 static void make_plan(Plan &p, int64_t N, int n) {
@@ -151,6 +205,7 @@ static bdss_status finish(bdss_ctx *h, bdss_info *info) {
   cudaError_t e = cudaMemcpyAsync(h->hst, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e);
+  kt_harvest(h);
   const int st = h->hst->status;
   if (h->hst->trace[0] != 0) {  // a launch with grid barriers: keep its stamps
     int c = 0;
@@ -208,7 +263,11 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
       }
     h->launches += 1;
     h->barriers += 1 + (factor ? 3 : 2) * p.L + ((rhs && p.L > 0) ? p.L : 0);
-    return launch_large_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid_for(h, most), h->smem, h->stream);
+    kt_begin(h, h->kt_cls);
+    const cudaError_t e = launch_large_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid_for(h, most), h->smem,
+                                                     h->stream);
+    kt_end(h, 1);
+    return e;
   }
   Args<T> b = a;
   if (!rhs) b.d = 0;
@@ -216,15 +275,21 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < p.L && e == cudaSuccess; ++l)
     for (int sub = factor ? 0 : 1; sub < 3 && e == cudaSuccess; ++sub) {
+      kt_begin(h, (tc_factor && sub == 2) ? BDSS_KT_SCHUR_TC : h->kt_cls);
       e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz, h->tf32)), h->smem,
                               h->stream);
+      kt_end(h, 1);
       h->launches += 1;
     }
+  kt_begin(h, h->kt_cls);
   if (e == cudaSuccess) e = launch_large_top<T>(b, f, h->smem, h->stream);
+  kt_end(h, 1);
   h->launches += 1;
   if (rhs)
     for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
+      kt_begin(h, h->kt_cls);
       e = launch_large_sub<T>(b, l, 3, 0, grid_for(h, large_sub_tasks(p, l, 3, 0, b.d, esz, 0)), h->smem, h->stream);
+      kt_end(h, 1);
       h->launches += 1;
     }
   return e;
@@ -246,11 +311,16 @@ static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool r
     int bars = 1 + 2 * p.L;  // the spread-rank barrier, then two per level
     if (rhs && p.L > 0) bars += 1 + (p.L - 1);
     h->barriers += bars;
-    return launch_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid, h->smem, h->stream);
+    kt_begin(h, h->kt_cls);
+    const cudaError_t e = launch_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid, h->smem, h->stream);
+    kt_end(h, 1);
+    return e;
   }
   Args<T> b = a;
   if (!rhs) b.d = 0;
   cudaError_t e = cudaSuccess;
+  kt_begin(h, h->kt_cls);  // the per-level launches of one pass as one group
+  const int64_t launches0 = h->launches;
   for (int l = 0; l < p.L && e == cudaSuccess; ++l) {
     const long long nElim = p.Nl[l] / 2, nSep = (p.Nl[l] + 1) / 2;
     e = launch_phaseA<T>(b, l, factor ? 1 : 0, grid_for(h, nElim * parts_A<T>(p, l, factor, cap)), h->smem,
@@ -267,6 +337,7 @@ static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool r
       e = launch_phaseC<T>(b, l, grid_for(h, p.Nl[l] / 2), h->smem, h->stream);
       h->launches += 1;
     }
+  kt_end(h, (int)(h->launches - launches0));
   return e;
 }
 
@@ -307,6 +378,7 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->kr_sc);
   cudaFree(h->dst);
   if (h->hst) cudaFreeHost(h->hst);
+  for (cudaEvent_t ev : h->kt_ev) cudaEventDestroy(ev);
   delete h;
   return BDSS_OK;
 }
@@ -420,6 +492,24 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
       if (value < 1 || value > 100000) return BDSS_ERR_INVALID_ARG;
       h->max_krylov = (int)value;
       return BDSS_OK;
+    case BDSS_OPT_KERNEL_TIMING:
+      if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
+      if (value && h->kt_ev.empty()) {
+        h->kt_ev.assign(2 * kKtPairs, nullptr);
+        for (auto &ev : h->kt_ev)
+          if (cudaEventCreate(&ev) != cudaSuccess) {
+            const cudaError_t err = cudaGetLastError();
+            for (auto &e2 : h->kt_ev)
+              if (e2) cudaEventDestroy(e2);
+            h->kt_ev.clear();
+            return cuda_fail(err);
+          }
+        h->kt_pair_cls.assign(kKtPairs, 0);
+        h->kt_pair_n.assign(kKtPairs, 0);
+      }
+      h->ktiming = (int)value;
+      kt_reset(h);
+      return BDSS_OK;
     case BDSS_OPT_DEBUG_CORRUPT_GUARD: {
       // test hook: overwrite one byte of buffer `value`'s guard band from the host
       if (value < 1 || value > (int64_t)h->guards.size()) return BDSS_ERR_INVALID_ARG;
@@ -495,6 +585,8 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
   h->factored = false;
   h->launches = 0;
   h->barriers = 0;
+  kt_reset(h);
+  h->kt_cls = BDSS_KT_FACTOR;
   const bool rhs = (B != nullptr);
   cudaError_t e = reset_status(h);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -538,11 +630,13 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
 static bdss_status residual_berr(bdss_ctx *h, const double *B, const double *X, int d, double *berr) {
   cudaError_t e = reset_status(h);
   const int with_norm = h->norm_valid ? 0 : 1;
+  kt_begin(h, BDSS_KT_RESIDUAL);
   if (e == cudaSuccess)
     e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
                                         (int)std::min<long long>(h->N, 2LL * h->sms), h->stream)
                  : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
                                    grid_for(h, h->N) * 2, h->stream);
+  kt_end(h, 1);
   h->launches += 1;
   if (e != cudaSuccess) return cuda_fail(e);
   bdss_status st = finish(h, nullptr);
@@ -583,6 +677,7 @@ static bdss_status apply_precond(bdss_ctx *h, int d) {
   a.Y = h->Y32;
   a.X64 = h->kr_Z;
   a.x_accumulate = 0;
+  h->kt_cls = BDSS_KT_KRYLOV;
   if (e == cudaSuccess) e = run_levels<float>(h, a, false, true);
   if (e != cudaSuccess) return cuda_fail(e);
   return finish(h, nullptr);
@@ -598,27 +693,34 @@ static bdss_status krylov_cycle(bdss_ctx *h, const double *B, double *X, int d) 
   const int gD = col_dots_grid(rows, d), gU = pcg_update_grid(rows);
   cudaStream_t s = h->stream;
   double *R = h->kr_R, *Z = h->kr_Z, *P = h->kr_P, *Q = h->kr_Q, *part = h->kr_part, *sc = h->kr_sc;
+  kt_begin(h, BDSS_KT_KRYLOV);
   cudaError_t e = launch_btd_apply(h->N, h->n, d, h->A_diag, h->A_sub, X, B, R, h->sms, s);  // r = B - A X
+  kt_end(h, 1);
   h->launches += 1;
   if (e != cudaSuccess) return cuda_fail(e);
   bdss_status st = apply_precond(h, d);
   if (st != BDSS_OK) return st;
+  kt_begin(h, BDSS_KT_KRYLOV);
   e = launch_col_dots(rows, d, Z, R, nullptr, nullptr, part, gD, s);
   if (e == cudaSuccess) e = launch_pcg_scalars(gD, d, part, kPcgStart, sc, s);
   if (e == cudaSuccess) e = launch_pcg_direction(rows, d, sc, Z, P, 1, h->sms, s);
+  kt_end(h, 3);
   h->launches += 3;
   if (e != cudaSuccess) return cuda_fail(e);
   double best = INFINITY;
   int since_best = 0;
   for (int k = 0; k < h->max_krylov; ++k) {
+    kt_begin(h, BDSS_KT_KRYLOV);
     e = launch_btd_apply(h->N, h->n, d, h->A_diag, h->A_sub, P, nullptr, Q, h->sms, s);  // q = A p
     if (e == cudaSuccess) e = launch_col_dots(rows, d, P, Q, nullptr, nullptr, part, gD, s);
     if (e == cudaSuccess) e = launch_pcg_scalars(gD, d, part, kPcgAlpha, sc, s);
     if (e == cudaSuccess) e = launch_pcg_update(rows, d, sc, P, Q, X, R, part, gU, s);
     if (e == cudaSuccess) e = launch_pcg_scalars(gU, d, part, kPcgNorms, sc, s);
     double nrm[2] = {0.0, 0.0};
+    kt_end(h, 5);
     if (e == cudaSuccess) e = cudaMemcpyAsync(nrm, sc + kScNorm, sizeof(nrm), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    kt_harvest(h);
     h->launches += 5;
     if (e != cudaSuccess) return cuda_fail(e);
     ++h->last_cg;
@@ -633,9 +735,11 @@ static bdss_status krylov_cycle(bdss_ctx *h, const double *B, double *X, int d) 
     }
     st = apply_precond(h, d);  // z = M^-1 r
     if (st != BDSS_OK) return st;
+    kt_begin(h, BDSS_KT_KRYLOV);
     e = launch_col_dots(rows, d, Z, R, Z, Q, part, gD, s);
     if (e == cudaSuccess) e = launch_pcg_scalars(gD, d, part, kPcgBeta, sc, s);
     if (e == cudaSuccess) e = launch_pcg_direction(rows, d, sc, Z, P, 0, h->sms, s);
+    kt_end(h, 3);
     h->launches += 3;
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -673,6 +777,7 @@ static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_i
       a.Y = h->Y32;
       a.X64 = X;
       a.x_accumulate = 1;
+      h->kt_cls = BDSS_KT_CORRECTION;
       if (e == cudaSuccess) e = run_levels<float>(h, a, false, true);
       if (e != cudaSuccess) return cuda_fail(e);
       st = finish(h, nullptr);
@@ -710,6 +815,8 @@ bdss_status bdss_solve(bdss_handle h, const double *B, double *X, int32_t d, bds
   if (!h->factored) return BDSS_ERR_NOT_FACTORED;
   h->launches = 0;
   h->barriers = 0;
+  kt_reset(h);
+  h->kt_cls = BDSS_KT_SOLVE;
   cudaError_t e = reset_status(h);
   if (e != cudaSuccess) return cuda_fail(e);
   if (!is_mixed(h)) {
@@ -859,6 +966,16 @@ bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity
   const int c = std::min(h->trace_count, (int)capacity);
   for (int i = 0; i < c; ++i) release_ns[i] = h->trace[i];
   if (count) *count = h->trace_count;
+  return BDSS_OK;
+}
+
+bdss_status bdss_last_kernel_times(bdss_handle h, double *ms, int64_t *launches, int32_t classes) {
+  if (!h || classes < 0 || (classes > 0 && !ms)) return BDSS_ERR_INVALID_ARG;
+  const int c = std::min((int)classes, (int)BDSS_KT_CLASSES);
+  for (int i = 0; i < c; ++i) {
+    ms[i] = h->kt_ms[i];
+    if (launches) launches[i] = h->kt_n[i];
+  }
   return BDSS_OK;
 }
 

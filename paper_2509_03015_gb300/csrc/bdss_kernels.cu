@@ -291,7 +291,7 @@ size_t smem_bytes(int n, int d) {
 // The dynamic shared-memory limit of every kernel is raised once to the
 // device's opt-in maximum, so that handles of different sizes never lower
 // it under one another; each launch still requests only what it needs.
-static cudaError_t raise_smem_limits() {
+cudaError_t raise_smem_limits() {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -313,9 +313,14 @@ static cudaError_t raise_smem_limits() {
 
 template <typename T>
 cudaError_t configure(int n, int d, size_t *smem, int *blocks_per_sm) {
-  const size_t sm = smem_bytes<T>(n, d);
   cudaError_t e0 = raise_smem_limits();
   if (e0 != cudaSuccess) return e0;
+  return occupancy<T>(n, d, smem, blocks_per_sm);
+}
+
+template <typename T>
+cudaError_t occupancy(int n, int d, size_t *smem, int *blocks_per_sm) {
+  const size_t sm = smem_bytes<T>(n, d);
   int occ = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persistent<T>, kThreads, sm);
   if (e != cudaSuccess) return e;
@@ -372,6 +377,7 @@ cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, d
 #define BDSS_INSTANTIATE(T)                                                                                   \
   template size_t smem_bytes<T>(int, int);                                                                    \
   template cudaError_t configure<T>(int, int, size_t *, int *);                                               \
+  template cudaError_t occupancy<T>(int, int, size_t *, int *);                                               \
   template cudaError_t launch_persistent<T>(const Args<T> &, int, int, int, size_t, cudaStream_t);            \
   template cudaError_t launch_phaseA<T>(const Args<T> &, int, int, int, size_t, cudaStream_t);                \
   template cudaError_t launch_phaseB<T>(const Args<T> &, int, int, int, size_t, cudaStream_t);                \

@@ -94,13 +94,13 @@ __global__ void __launch_bounds__(kThreads) BDSS_LARGE_MAXNREG(T)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_flag;
   if constexpr (kTc) {
-    __shared__ uint64_t s_bars[2];
+    __shared__ uint64_t s_bars[3];
     __shared__ uint32_t s_tmem;
     TcState tc;
     const bool use_tc = a.tf32 && factor;
     if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
     large_body<T, true>(a, factor, rhs, smem_raw, &s_flag, use_tc ? &tc : nullptr);
-    if (use_tc) tc_end(tc);
+    if (use_tc) tc_end(tc, a.timeout_ns);
   } else {
     large_body<T, false>(a, factor, rhs, smem_raw, &s_flag, nullptr);
   }
@@ -113,14 +113,14 @@ __global__ void __launch_bounds__(kThreads) BDSS_LARGE_MAXNREG(T)
   __shared__ int s_flag;
   if (ld_relaxed_i32(&a.st->status) != 0) return;
   if constexpr (kTc) {
-    __shared__ uint64_t s_bars[2];
+    __shared__ uint64_t s_bars[3];
     __shared__ uint32_t s_tmem;
     TcState tc;
     const bool use_tc = a.tf32 && factor && sub == kSubB;
     if (use_tc) tc_begin(tc, smem_raw, s_bars, &s_tmem);
     large_sub<T, true>(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, use_tc ? &tc : nullptr,
                        (int)blockIdx.x);
-    if (use_tc) tc_end(tc);
+    if (use_tc) tc_end(tc, a.timeout_ns);
   } else {
     large_sub<T, false>(a, l, sub, factor != 0, reinterpret_cast<T *>(smem_raw), &s_flag, nullptr, (int)blockIdx.x);
   }
@@ -334,7 +334,7 @@ cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows,
 __global__ void __launch_bounds__(kThreads) k_tc_selftest(const __grid_constant__ CUtensorMap map, const float *W,
                                                           int n, double *err, int *status, long long timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint64_t s_bars[2];
+  __shared__ uint64_t s_bars[3];
   __shared__ uint32_t s_tmem;
   TcState tc;
   tc_begin(tc, smem_raw, s_bars, &s_tmem);
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_selftest(const __grid_constant_
     }
     atomicMax(reinterpret_cast<unsigned long long *>(err), (unsigned long long)__double_as_longlong(worst));
   }
-  tc_end(tc);
+  tc_end(tc, timeout_ns);
 }
 
 cudaError_t run_tc_selftest(double *max_err, int *status) {

@@ -8,7 +8,12 @@
 namespace bdss {
 
 template <typename T> size_t smem_bytes(int n, int d);
+// configure = raise_smem_limits (every kernel's dynamic shared-memory limit
+// to the device's opt-in maximum) + occupancy (shared memory per CTA and
+// resident CTAs per SM of the persistent kernel for (n, d)).
 template <typename T> cudaError_t configure(int n, int d, size_t *smem, int *blocks_per_sm);
+cudaError_t raise_smem_limits();
+template <typename T> cudaError_t occupancy(int n, int d, size_t *smem, int *blocks_per_sm);
 template <typename T>
 cudaError_t launch_persistent(const Args<T> &a, int factor, int rhs, int grid, size_t smem, cudaStream_t s);
 template <typename T>

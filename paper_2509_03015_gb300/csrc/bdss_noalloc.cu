@@ -31,28 +31,60 @@ constexpr int kMaxDevices = 64;
 // The shared scratch: status word, factors, coupling slots, top factor.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device.  In host code `g_scratch` names a
-// host-side stand-in, never the device memory, so it is only ever used via
-// cudaGetSymbolAddress.
-static void *g_scratch_dev[kMaxDevices];
-static bool g_ready[kMaxDevices];
+// Per-device set-up: the device address of g_scratch (in host code
+// `g_scratch` names a host-side stand-in, never the device memory, so it is
+// only ever used via cudaGetSymbolAddress), the SM count and the opt-in
+// shared-memory limit.
+struct DeviceSetup {
+  void *scratch = nullptr;
+  int sms = 0;
+  int smem_optin = 0;
+  bool ready = false;
+};
+static DeviceSetup g_dev[kMaxDevices];
 static std::mutex g_setup_mutex;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Once per device, with that device current: look up the array's device
-// address and raise the kernels' shared-memory limits.
-cudaError_t setup_device(int dev, void **out) {
+// address and the device's limits, and raise the kernels' shared-memory
+// limits, so that later calls make no attribute calls.
+cudaError_t setup_device(int dev, DeviceSetup *out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_ready[dev]) {
+  DeviceSetup &g = g_dev[dev];
+  if (!g.ready) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = raise_smem_limits();
     if (e != cudaSuccess) return e;
-    g_scratch_dev[dev] = p;
-    g_ready[dev] = true;
+    g.scratch = p;
+    g.ready = true;
   }
-  *out = g_scratch_dev[dev];
+  *out = g;
   return cudaSuccess;
+}
+
+// Can the device read p in place (device, managed or mapped page-locked
+// memory, or any host memory where the device reads pageable memory)?  With
+// `write`, only device and managed memory qualify.
+bool device_accessible(const void *p, bool write) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+  if (write) return false;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
+  int dev = 0, pageable = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return pageable != 0;
 }
 
 void make_plan_noalloc(Plan &p, int64_t N, int n) {
@@ -81,8 +113,10 @@ extern "C" bdss_status bdss_factor_solve_noalloc(int64_t N, int32_t n, int32_t d
     info->reserved = 0;
     info->backward_err = -1.0;
   }
-  if (N < 1 || n < 1 || n > kMaxN || d < 1 || d > 64) return BDSS_ERR_INVALID_ARG;
-  if (N > ((int64_t)1 << (kMaxLevels - 2))) return BDSS_ERR_INVALID_ARG;
+  if (N < 1 || n < 1 || d < 1 || d > 64) return BDSS_ERR_INVALID_ARG;
+  // blocks up to n = 64 only (the shared-memory path); longer horizons than
+  // the level plan holds are beyond the scratch anyway
+  if (n > kMaxN || N > ((int64_t)1 << (kMaxLevels - 2))) return BDSS_ERR_UNSUPPORTED;
   if (!A_diag || !B || !X || (N > 1 && !A_sub)) return BDSS_ERR_INVALID_ARG;
   if ((((uintptr_t)A_diag | (uintptr_t)A_sub | (uintptr_t)B | (uintptr_t)X) & 15u) != 0)
     return BDSS_ERR_INVALID_ARG;
@@ -99,16 +133,19 @@ extern "C" bdss_status bdss_factor_solve_noalloc(int64_t N, int32_t n, int32_t d
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BDSS_ERR_CUDA;
-  void *base = nullptr;
-  e = setup_device(dev, &base);
+  DeviceSetup g;
+  e = setup_device(dev, &g);
   if (e != cudaSuccess) return BDSS_ERR_CUDA;
+  if (!device_accessible(A_diag, false) || !device_accessible(B, false) || !device_accessible(X, true) ||
+      (N > 1 && !device_accessible(A_sub, false)))
+    return BDSS_ERR_INVALID_ARG;
+  if (smem_bytes<double>(n, d) > (size_t)g.smem_optin) return BDSS_ERR_UNSUPPORTED;
   size_t smem = 0;
-  int bps = 0, sms = 0;
-  e = configure<double>(n, d, &smem, &bps);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int bps = 0;
+  e = occupancy<double>(n, d, &smem, &bps);
   if (e != cudaSuccess || bps < 1) return BDSS_ERR_CUDA;
 
-  unsigned char *p = (unsigned char *)base;
+  unsigned char *p = (unsigned char *)g.scratch;
   DevStatus *st = (DevStatus *)p;
   Args<double> a;
   memset(&a, 0, sizeof(a));
@@ -123,13 +160,21 @@ extern "C" bdss_status bdss_factor_solve_noalloc(int64_t N, int32_t n, int32_t d
   a.Y = X;
   a.st = st;
   a.timeout_ns = 10000000000LL;
+  // as bdss_create: tail levels with fewer blocks than resident CTAs split
+  // each block's work over several CTAs (same arithmetic, same result)
+  a.capacity = bps * g.sms;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the status word and barrier counters must start at zero; the rest of the
   // scratch is written before it is read
   e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-  long long grid = (long long)bps * sms;
-  if ((N + 1) / 2 < grid) grid = (N + 1) / 2;
-  if (grid < 1) grid = 1;
+  long long most = 1;  // tasks of the busiest step, as bdss_factor_solve sizes its grid
+  for (int l = 0; l < plan.L; ++l) {
+    const long long tA = (plan.Nl[l] / 2) * parts_A<double>(plan, l, true, a.capacity);
+    const long long tB = ((plan.Nl[l] + 1) / 2) * parts_B<double>(plan, l, true, a.capacity);
+    if (tA > most) most = tA;
+    if (tB > most) most = tB;
+  }
+  const long long grid = most < a.capacity ? most : a.capacity;
   if (e == cudaSuccess) e = launch_persistent<double>(a, 1, 1, (int)grid, smem, s);
   DevStatus h;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);

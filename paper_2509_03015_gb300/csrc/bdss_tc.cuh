@@ -50,6 +50,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
   }
 }
 
+// CTA-uniform bounded wait (all threads call it): thread 0 polls with the
+// time limit and broadcasts the outcome through shared memory, so every
+// thread takes the same branch afterwards; on success each thread then
+// observes the completed phase itself (its wait returns at once), which makes
+// the asynchronous writes of that phase visible to it.
+__device__ __forceinline__ bool mbar_wait_cta(uint64_t *bar, uint32_t parity, long long timeout_ns, int *s_ok) {
+  if (threadIdx.x == 0) *s_ok = mbar_wait(bar, parity, timeout_ns) ? 1 : 0;
+  __syncthreads();
+  const bool ok = *s_ok != 0;
+  if (ok && threadIdx.x != 0) mbar_wait(bar, parity, timeout_ns);
+  __syncthreads();  // *s_ok is read by all before thread 0 may write it again
+  return ok;
+}
+
 // ---- TMA -------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
   asm volatile(
@@ -129,9 +143,11 @@ struct TcState {
   unsigned char *slab;   // 1024-aligned: A hi | A lo | B hi | B lo
   uint64_t *bar_tma;     // TMA completion
   uint64_t *bar_mma;     // MMA completion
+  int *s_ok;             // shared word of mbar_wait_cta
   uint32_t tmem;         // TMEM base address (128 columns)
   uint32_t ph_tma, ph_mma;
-  bool ok;
+  bool tma_pending;      // a TMA load or an MMA batch was issued and its
+  bool mma_pending;      // completion has not been observed (CTA-uniform)
 };
 
 // Split the staged FP32 values of a slab in place into TF32 hi (rounded to
@@ -170,7 +186,9 @@ __device__ __forceinline__ bool tc_accumulate(TcState &s, const CUtensorMap *map
       tma_load_2d(Ahi, map, k0, ra, s.bar_tma);
       tma_load_2d(Bhi, map, k0, rb, s.bar_tma);
     }
-    if (!mbar_wait(s.bar_tma, s.ph_tma, timeout_ns)) return false;
+    s.tma_pending = true;
+    if (!mbar_wait_cta(s.bar_tma, s.ph_tma, timeout_ns, s.s_ok)) return false;
+    s.tma_pending = false;
     s.ph_tma ^= 1;
     tc_split_slab(Ahi, Alo);
     tc_split_slab(Bhi, Blo);
@@ -188,9 +206,10 @@ __device__ __forceinline__ bool tc_accumulate(TcState &s, const CUtensorMap *map
       }
       tc_commit(s.bar_mma);
     }
-    if (!mbar_wait(s.bar_mma, s.ph_mma, timeout_ns)) return false;
+    s.mma_pending = true;
+    if (!mbar_wait_cta(s.bar_mma, s.ph_mma, timeout_ns, s.s_ok)) return false;
+    s.mma_pending = false;
     s.ph_mma ^= 1;
-    __syncthreads();
   }
   return true;
 }
@@ -213,14 +232,18 @@ __device__ __forceinline__ void tc_read_row(const TcState &s, float (&v)[64], in
   }
 }
 
-// Set up mbarriers (in static shared memory, `bars` = 2 words, so that other
-// phases reusing the dynamic shared memory cannot clobber them) and TMEM
-// (warp 0 allocates); call with all threads.
+// Set up mbarriers (in static shared memory, `bars` = 3 words: the two
+// barriers and the flag word of mbar_wait_cta, so that other phases reusing
+// the dynamic shared memory cannot clobber them) and TMEM (warp 0
+// allocates); call with all threads.
 __device__ __forceinline__ void tc_begin(TcState &s, unsigned char *smem_base, uint64_t *bars, uint32_t *tmem_slot) {
   const uintptr_t p = (reinterpret_cast<uintptr_t>(smem_base) + 1023) & ~(uintptr_t)1023;
   s.slab = reinterpret_cast<unsigned char *>(p);
   s.bar_tma = bars;
   s.bar_mma = bars + 1;
+  s.s_ok = reinterpret_cast<int *>(bars + 2);
+  s.tma_pending = false;
+  s.mma_pending = false;
   if (threadIdx.x == 0) {
     mbar_init(s.bar_tma, 1);
     mbar_init(s.bar_mma, 1);
@@ -233,10 +256,15 @@ __device__ __forceinline__ void tc_begin(TcState &s, unsigned char *smem_base, u
   s.tmem = *tmem_slot;
   s.ph_tma = 0;
   s.ph_mma = 0;
-  s.ok = true;
 }
 
-__device__ __forceinline__ void tc_end(TcState &s) {
+// Release TMEM (all threads call it).  After a timed-out wait, first wait
+// again, with the same kind of limit, for the load or MMA batch still in
+// flight, so that nothing writes the shared memory or TMEM being released;
+// TMEM is freed whether or not that second wait completes.
+__device__ __forceinline__ void tc_end(TcState &s, long long timeout_ns) {
+  if (s.tma_pending && mbar_wait_cta(s.bar_tma, s.ph_tma, timeout_ns, s.s_ok)) s.tma_pending = false;
+  if (s.mma_pending && mbar_wait_cta(s.bar_mma, s.ph_mma, timeout_ns, s.s_ok)) s.mma_pending = false;
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) tmem_dealloc(s.tmem, 128);

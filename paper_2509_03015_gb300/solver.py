@@ -126,6 +126,15 @@ class Solver:
                    "bdss_last_refine_stats")
         return p.value, c.value
 
+    def kernel_times(self):
+        """{class: (ms, launches)} of the last call, timed with CUDA events on
+        the handle's stream (set_option("kernel_timing", 1) first)."""
+        k = len(_lib.KERNEL_CLASSES)
+        ms = (ctypes.c_double * k)()
+        n = (ctypes.c_int64 * k)()
+        _lib.check(self.lib.bdss_last_kernel_times(self.h, ms, n, k), "bdss_last_kernel_times")
+        return {c: (ms[i], n[i]) for i, c in enumerate(_lib.KERNEL_CLASSES)}
+
     def launch_config(self):
         """(resident CTAs per SM, SM count, dynamic shared memory bytes per
         CTA) of this handle's persistent kernel."""

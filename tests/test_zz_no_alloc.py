@@ -1,10 +1,12 @@
 """The no-allocation entry point (bdss_factor_solve_noalloc), called through
 the C ABI, must give the same solution as the allocating entry point
 (bdss_create + bdss_factor_solve) within the parity tolerance used elsewhere,
-on two calls in a row with different systems (so that what the first call
-leaves in the shared scratch cannot leak into the second).  It serves callers
-that may not allocate device memory while they run, such as a real-time
-control loop or a plugin whose host owns all device memory.
+and meet the oracle's forward- and backward-error bars, on calls in a row
+with different systems (so that what one call leaves in the shared scratch
+cannot leak into the next).  One system has n >= 32, so the tail levels split
+blocks over CTAs as the allocating entry point does.  It serves callers that
+may not allocate device memory while they run, such as a real-time control
+loop or a plugin whose host owns all device memory.
 
 Kept in a file of its own, collected last."""
 import ctypes
@@ -53,17 +55,20 @@ def _rel(X, Y):
     return np.abs(X - Y).sum(axis=-1).max() / np.abs(Y).sum(axis=-1).max()
 
 
-def test_noalloc_matches_allocating_entry_point_twice():
+def test_noalloc_matches_allocating_entry_point_twice(oracle_mod):
     from paper_2509_03015_gb300 import _lib
     lib = _lib.load()
-    s1 = inputs.random_btd(300, 16, 2, seed=21)
-    s2 = inputs.workload("kalman-N64-n8-d1")
-    for s in (s1, s2):
+    systems = [inputs.random_btd(300, 16, 2, seed=21), inputs.workload("kalman-N64-n8-d1"),
+               inputs.random_btd(300, 48, 2, seed=22)]
+    for s in systems:
         st, X = _noalloc(lib, s)
         assert st == 0, _lib.STATUS_NAMES.get(st)
         Xr = _allocating(s)
         assert np.all(np.isfinite(X))
         assert _rel(X, Xr) <= FWD_TOL
+        Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
+        assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+        assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= 1e-14
 
 
 def test_noalloc_rejects_systems_beyond_its_scratch():
@@ -74,3 +79,7 @@ def test_noalloc_rejects_systems_beyond_its_scratch():
     st = lib.bdss_factor_solve_noalloc(4096, 64, 1, ctypes.c_void_p(16), ctypes.c_void_p(16),
                                        ctypes.c_void_p(16), ctypes.c_void_p(16), None, ctypes.byref(info))
     assert st == 8  # BDSS_ERR_UNSUPPORTED, returned before any launch
+    # blocks beyond n = 64 (the tiled path) are not offered without allocation
+    st = lib.bdss_factor_solve_noalloc(4, 96, 1, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                       ctypes.c_void_p(16), ctypes.c_void_p(16), None, ctypes.byref(info))
+    assert st == 8
