@@ -16,7 +16,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -31,8 +30,13 @@ sys.path.insert(0, ROOT)
 from paper_2509_03015_gb300 import accounting, inputs  # noqa: E402
 
 WORKLOAD = "kalman-N16384-n64-d4"
+MIXED_WORKLOAD = "kalman-N4096-n256-d16-rho0.99"
 METRIC = "systems/sec & % roofline, factor+solve; FP32+refine vs FP64 at backward err<=1e-14"
-PROFILE = os.path.join(ROOT, "profiles", "k_persistent_fp64_kalman-N16384-n64-d4.md")
+# DRAM traffic of the headline kernel from an ncu capture (small data file
+# beside its summary): bytes per block processed and the digest of the kernel
+# sources it was taken on
+TRAFFIC = os.path.join(ROOT, "profiles", "k_persistent_fp64_kalman-N16384-n64-d4.traffic.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CSRC = os.path.join(ROOT, "paper_2509_03015_gb300", "csrc")
 L2_BYTES = 129 * 2 ** 20
 
@@ -52,22 +56,120 @@ def csrc_digest():
 
 
 def profiled_traffic(N):
-    """DRAM bytes per launch from the committed ncu summary, scaled by the
-    blocks processed; None if the kernels changed since the capture."""
+    """DRAM bytes per launch from the committed ncu capture's data file,
+    scaled by the blocks processed; None if the kernels changed since."""
     try:
-        txt = open(PROFILE).read()
-    except OSError:
+        with open(TRAFFIC) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
-    m1 = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", txt)
-    m2 = re.search(r"dram_bytes_per_block:\s*([0-9.eE+]+)", txt)
-    if not m1 or not m2 or m1.group(1) != csrc_digest():
+    if rec.get("kernel_sources_sha256") != csrc_digest():
         return None
-    return float(m2.group(1)) * N
+    return float(rec["dram_bytes_per_block"]) * N
 
 
 def fp64_peak(sms, mhz):
     """FP64 ALU peak: SMs x 2 DFMA/clk/SM x 2 flop x clock (GB300 FP64 rate)."""
     return sms * 2 * 2 * mhz * 1e6
+
+
+def fp32_peak(sms, mhz):
+    """FP32 ALU peak: SMs x 128 FFMA lanes x 2 flop x clock."""
+    return sms * 128 * 2 * mhz * 1e6
+
+
+def measured_peaks():
+    """HBM GB/s and dense BF16 TFLOP/s measured on the GB300s (file
+    written by the driver), else the earlier measurement's figures."""
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "bf16_tflops_sustained": float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def kernel_rooflines(kt, N, n, d, mode, sms, mhz):
+    """Roofline of each kernel class of one mixed-precision (or FP64) step from
+    its CUDA-event times: kt = {class: (ms, launches)} summed over the timed
+    steps.  Work per launch (algorithmic):
+      residual    6 n^2 d N flops (three n x n blocks times d columns per block
+                  row), FP64 ALU;
+      correction  the stored factors streamed up and down once each:
+                  2 x 4 B x (N + slots) n^2, plus X (FP64, read + write) and the
+                  FP32 residual: HBM;
+      factor      the oracle's block-Thomas tally of factor + solve, on the
+                  ALU of the mode's precision;
+      schur_tc    the Schur products of every level as tensor-core tiles
+                  (accounting.tc_tile_flops, one product counted once; the
+                  3xTF32 split executes three), TF32 tensor rate = measured
+                  BF16 x 1/2 (nominal ratio)."""
+    pk = measured_peaks()
+    out = {}
+    slots = sum(Nl - 1 for Nl in accounting.levels(N)[:-1])
+    esz = 8 if mode == "fp64" else 4
+    for cls, (ms, launches) in kt.items():
+        if launches <= 0 or ms <= 0:
+            continue
+        per = ms / launches * 1e-3
+        if cls == "residual":
+            work, unit, bound = 6.0 * n * n * d * N, "TFLOP/s", "alu"
+            peak, pdef = fp64_peak(sms, mhz), "FP64 ALU (SMs x 2 DFMA/clk x 2 x clock)"
+        elif cls == "correction":
+            work = 2.0 * esz * (N + slots) * n * n + 8.0 * N * n * d * 2 + 4.0 * N * n * d
+            unit, bound = "GB/s", "hbm"
+            peak, pdef = pk["hbm_gbs"] * 1e9, f"HBM copy bandwidth ({pk['source']})"
+        elif cls == "schur_tc":
+            work, unit, bound = accounting.tc_tile_flops(N, n), "TFLOP/s", "tensor"
+            peak = pk["bf16_tflops"] * 0.5e12
+            pdef = f"TF32 dense = BF16 ({pk['source']}) x 1/2 nominal ratio"
+        elif cls == "factor":
+            t = accounting.thomas_flops(N, n, d)
+            work, unit, bound = t["factor"] + t["solve"], "TFLOP/s", "alu"
+            peak = fp64_peak(sms, mhz) if mode == "fp64" else fp32_peak(sms, mhz)
+            pdef = "FP64 ALU" if mode == "fp64" else "FP32 ALU (SMs x 128 FFMA x 2 x clock)"
+        else:
+            continue
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = work / per
+        out[cls] = {"bound": bound, "achieved": ach / scale, "peak": peak / scale, "unit": unit,
+                    "frac": ach / peak, "launch_ms": per * 1e3, "launches": launches,
+                    "work_per_launch": work, "peak_definition": pdef}
+        if cls == "schur_tc":
+            out[cls]["executed_frac"] = 3 * ach / peak
+    return out
+
+
+def _oracle_solve_to_file(name, path):
+    """Child process: the oracle's X for a named workload, saved as .npy."""
+    import oracle
+    oracle.build()
+    s = inputs.workload(name)
+    np.save(path, oracle.solve_system(s["A_diag"], s["A_sub"], s["B"]))
+
+
+def start_oracle_job(name):
+    """Start the oracle solve of `name` in a spawned process (started before
+    any CUDA call; it runs on one host core while the GPU legs run)."""
+    import multiprocessing as mp
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    proc = mp.get_context("spawn").Process(target=_oracle_solve_to_file, args=(name, path), daemon=True)
+    proc.start()
+    return proc, path
+
+
+def finish_oracle_job(job, timeout_s=600):
+    proc, path = job
+    proc.join(timeout_s)
+    try:
+        return np.load(path) if proc.exitcode == 0 else None
+    finally:
+        if proc.is_alive():
+            proc.terminate()
+        os.unlink(path)
 
 
 class ClockSampler:
@@ -179,7 +281,27 @@ def _timed(fn, reps, stream, max_over_ranks):
     return max_over_ranks(e0.elapsed_time(e1)) / reps
 
 
-def other_workloads(dev, stream, world, max_over_ranks, args):
+def timed_leg(sol, call, reps, stream, max_over_ranks, N, n, d, mode, sms, mhz):
+    """Time `call` (one factor + solve through the solver's handle) reps times
+    with the library's per-kernel CUDA events on, and return the step time,
+    the per-class times and their rooflines."""
+    sol.set_option("kernel_timing", 1)
+    kt = {}
+
+    def step():
+        call()
+        for c, (ms, k) in sol.kernel_times().items():
+            a = kt.get(c, (0.0, 0))
+            kt[c] = (a[0] + ms, a[1] + k)
+    ms = _timed(step, reps, stream, max_over_ranks)
+    sol.set_option("kernel_timing", 0)
+    per_step = {c: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for c, v in kt.items() if v[1]}
+    roof = kernel_rooflines(kt, N, n, d, mode, sms, mhz)
+    dom = max(per_step, key=lambda c: per_step[c]["ms_per_step"]) if per_step else None
+    return ms, per_step, roof, dom
+
+
+def other_workloads(dev, stream, world, max_over_ranks, args, oracle_job=None):
     """The other hot-path workloads on the same GPU: the N=4096, n=256, d=16
     mixed-precision system (FP32 + refinement vs FP64), the 512-instance
     uneven MPC batch in one launch, forward + adjoint backward at
@@ -209,17 +331,36 @@ def other_workloads(dev, stream, world, max_over_ranks, args):
     X = torch.empty_like(B)
     entry = {"N": cfg["N"], "n": cfg["n"], "d": cfg["d"], "rho": cfg["rho"]}
     tally = accounting.thomas_flops(cfg["N"], cfg["n"], cfg["d"])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    Xs = {}
     for prec in ("tf32_ir", "fp32_ir", "fp64"):
         sol = Solver(cfg["N"], cfg["n"], d_max=cfg["d"], precision=prec, stream=stream)
         sol.factor_solve(Ad, As, B, X)
-        ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 1 if prec == "fp64" else reps, stream, max_over_ranks)
+        ms, kt, roof, dom = timed_leg(sol, lambda: sol.factor_solve(Ad, As, B, X), 1 if prec == "fp64" else reps,
+                                      stream, max_over_ranks, cfg["N"], cfg["n"], cfg["d"], prec, sms, args.mhz)
         info = sol.last_info
+        plain, cg = sol.refine_stats()
         entry[prec] = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms,
                        "thomas_tflops": (tally["factor"] + tally["solve"]) / (ms * 1e-3) / 1e12,
-                       "refine_iters": info.iters, "backward_err": info.backward_err}
+                       "refine_iters": info.iters, "refine_plain_steps": plain, "refine_cg_iters": cg,
+                       "backward_err": info.backward_err, "kernels": kt, "rooflines": roof,
+                       "roofline": dict(roof.get(dom, {}), kernel_class=dom) if dom else None}
+        Xs[prec] = X.cpu().numpy()
         sol.close()
     entry["speedup_fp32_ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["fp32_ir"]["ms_per_step"]
     entry["speedup_tf32_ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["tf32_ir"]["ms_per_step"]
+    if oracle_job is not None:
+        # error of every result against the FP64 oracle (computed outside the
+        # timed region, in a host process started before the GPU legs)
+        Xo = finish_oracle_job(oracle_job)
+        for prec, Xp in Xs.items():
+            if Xo is None:
+                entry[prec]["forward_err_vs_oracle"] = None
+                continue
+            diff = np.abs(Xp - Xo)
+            entry[prec]["forward_err_vs_oracle"] = float(diff.reshape(-1, Xo.shape[-1]).sum(1).max()
+                                                         / np.abs(Xo).reshape(-1, Xo.shape[-1]).sum(1).max())
+            entry[prec]["max_elementwise_err_vs_oracle"] = float(diff.max() / np.abs(Xo).max())
     res[name] = entry
     del Ad, As, B, X
     # -- batched MPC systems -----------------------------------------------------
@@ -355,21 +496,20 @@ def run_reference(args, world, rank):
     cfg = inputs.WORKLOADS[WORKLOAD]
     s = inputs.workload(WORKLOAD)
     N = s["A_diag"].shape[0]
-    Ns = 1024
 
     def step():
-        oracle.solve_system(s["A_diag"][:Ns], s["A_sub"][:Ns - 1], s["B"][:Ns])
+        oracle.solve_system(s["A_diag"], s["A_sub"], s["B"])
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     el = time.perf_counter() - t0
-    value = args.steps * (Ns / N) / el
-    sample = f"block-Thomas factor+solve of the first {Ns} of {N} blocks per step, scaled by {N}/{Ns}"
+    value = args.steps / el
+    sample = f"block-Thomas factor+solve of the whole system ({N} blocks) per step, one core"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps * (N / Ns),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "n": cfg["n"], "d": cfg["d"], "m": cfg["m"], "rho": cfg["rho"],
                    "seed": cfg["seed"], "path": "CPU FP64 block-Thomas oracle on the host cores",
@@ -377,6 +517,31 @@ def run_reference(args, world, rank):
         "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def run_case(args):
+    """Profiling mode: one named workload through the library, --reps calls,
+    one line per call (the ncu captures in profiles/ run this)."""
+    import torch
+
+    from paper_2509_03015_gb300 import Solver
+    cfg = dict(inputs.WORKLOADS[args.case])
+    if args.N is not None:
+        cfg["N"] = args.N
+    s = inputs.kalman_btd(cfg["N"], cfg["n"], cfg["m"], cfg["d"], cfg["rho"], cfg["seed"])
+    dev = torch.device("cuda:0")
+    Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
+    sol = Solver(cfg["N"], cfg["n"], d_max=cfg["d"], precision=args.precision, persistent=not args.per_level)
+    X = torch.empty_like(B)
+    for _ in range(args.reps):
+        t0 = time.perf_counter()
+        sol.factor_solve(Ad, As, B, X)
+        torch.cuda.synchronize()
+        info = sol.last_info
+        print(f"{args.case} N={cfg['N']} {args.precision} per_level={args.per_level}: "
+              f"{1e3 * (time.perf_counter() - t0):.2f} ms, iters {info.iters}, berr {info.backward_err:.2e}, "
+              f"launches {sol.launch_stats()[0]}")
+    sol.close()
 
 
 def phase_split(stamps, L, launch_ms):
@@ -405,11 +570,24 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed / per-level / e2e legs")
     ap.add_argument("--N", type=int, default=None,
                     help="horizon override (same generator) for small profiling cases")
+    ap.add_argument("--case", default=None, choices=sorted(inputs.WORKLOADS),
+                    help="profiling mode: run this workload --reps times and print one line per call")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "tf32_ir"])
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--per-level", action="store_true", help="profiling mode: one launch per level and phase")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
+    if args.case is not None:
+        run_case(args)
+        return
+    # the oracle's solution of the n = 256 workload, for the error of every
+    # mixed-precision result against it: started before any CUDA call
+    oracle_job = None
+    if not args.no_extras and args.N is None and world == 1 and not args.no_cpu_baseline:
+        oracle_job = start_oracle_job(MIXED_WORKLOAD)
 
     import torch
     import torch.distributed as dist
@@ -499,24 +677,23 @@ def main():
         "phase_us": phases,
     }
 
+    args.mhz = peak_mhz
     if not args.no_extras:
-        # FP32 factors + FP64 residual refinement on the same system
+        # FP32 factors + FP64 residual refinement on the same system, with the
+        # per-kernel CUDA-event times and the roofline of each kernel class
         mixed = Solver(N, n, d_max=d, precision="fp32_ir", stream=stream)
         X2 = torch.empty_like(B)
         for _ in range(max(1, args.warmup)):
             mixed.factor_solve(Ad, As, B, X2)
         K2 = max(3, args.steps // 2)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(K2):
-            mixed.factor_solve(Ad, As, B, X2)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms2 = max_over_ranks(e0.elapsed_time(e1)) / K2
+        ms2, kt2, roof2, dom2 = timed_leg(mixed, lambda: mixed.factor_solve(Ad, As, B, X2), K2, stream,
+                                          max_over_ranks, N, n, d, "fp32_ir", sm_count, peak_mhz)
         info = mixed.last_info
         out["fp32_ir"] = {"value": world * 1e3 / ms2, "unit": "systems/s", "ms_per_step": ms2,
                           "refine_iters": info.iters, "backward_err": info.backward_err,
-                          "speedup_vs_fp64": (elapsed_ms / args.steps) / ms2}
+                          "speedup_vs_fp64": (elapsed_ms / args.steps) / ms2, "kernels": kt2,
+                          "rooflines": roof2,
+                          "roofline": dict(roof2.get(dom2, {}), kernel_class=dom2) if dom2 else None}
         mixed.close()
         # the per-level launch structure (one launch per level and phase)
         per = Solver(N, n, d_max=d, precision="fp64", stream=stream, persistent=False)
@@ -571,7 +748,8 @@ def main():
         out["e2e"]["staged"]["path"] = "explicit host-to-device copies, then the device-input call; X copied back"
 
     if not args.no_extras and args.N is None:
-        out["workloads"] = other_workloads(dev, stream, world, max_over_ranks, args)
+        out["workloads"] = other_workloads(dev, stream, world, max_over_ranks, args, oracle_job)
+        oracle_job = None
         out["paper_shapes"] = paper_shapes(dev, stream, max_over_ranks)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -579,6 +757,8 @@ def main():
         if "workloads" in out:
             for name, r in cpu_rates().items():
                 out["workloads"].setdefault(name, {})["cpu_oracle"] = r
+    if oracle_job is not None:
+        finish_oracle_job(oracle_job, timeout_s=0)
     solver.close()
     if rank == 0:
         print(json.dumps(out))

@@ -51,3 +51,16 @@ def thomas_flops(N: int, n: int, d: int):
     fac = N * chol_flops(n) + (N - 1) * (n ** 3 + n * n * (n + 1))
     sol = N * 2.0 * n * n * d + (N - 1) * 4.0 * n * n * d
     return dict(factor=fac, solve=sol)
+
+
+def tc_tile_flops(N: int, n: int) -> float:
+    """Flops of the Schur-update products (Algorithm 3, Eq. 5) that the TF32
+    mode of the tiled path runs on the tensor cores, summed over the levels:
+    per separator one symmetric product n^2 (n+1) per eliminated neighbour and
+    the new coupling 2 n^3 when it exists (the separator part of cr_flops)."""
+    fl = 0.0
+    for Nl in levels(N)[:-1]:
+        for s in range(0, Nl, 2):
+            nb = (1 if s >= 2 else 0) + (1 if s + 1 < Nl else 0)
+            fl += nb * n * n * (n + 1) + (2 * n ** 3 if s + 2 < Nl else 0)
+    return fl

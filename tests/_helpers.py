@@ -48,3 +48,20 @@ def frac_solve(A, B):
 
 def frac_matmul(A, X):
     return [[sum(a * x for a, x in zip(row, col)) for col in zip(*X)] for row in A]
+
+
+def assert_elementwise(X, X_ref, rtol, atol_frac):
+    """Element by element: |X - X_ref| <= rtol |X_ref| + atol_frac max|X_ref|
+    for every entry, so that no single entry can be far off while a norm of
+    the difference stays small."""
+    X = np.asarray(X)
+    X_ref = np.asarray(X_ref)
+    assert X.shape == X_ref.shape
+    scale = float(np.abs(X_ref).max()) if X_ref.size else 0.0
+    err = np.abs(X - X_ref)
+    bound = rtol * np.abs(X_ref) + atol_frac * scale
+    bad = err > bound
+    if bad.any():
+        i = np.unravel_index(int(np.argmax(err - bound)), err.shape)
+        raise AssertionError(f"{int(bad.sum())} entries beyond tolerance; worst at {i}: got {X[i]!r}, "
+                             f"expected {X_ref[i]!r} (|diff| {err[i]:.3e} > {bound[i]:.3e})")

@@ -36,3 +36,14 @@ def test_cr_over_thomas_ratio():
     # block-Thomas factor flops for large N
     r = accounting.cr_flops(16384, 64, 4)["factor"] / accounting.thomas_flops(16384, 64, 4)["factor"]
     assert 2.6 < r < 2.75
+
+
+@pytest.mark.parametrize("N,n", [(1, 4), (2, 3), (9, 5), (100, 7)])
+def test_tc_tile_flops_is_the_separator_part_of_cr(N, n):
+    """The tensor-core Schur products are cr_flops' factor count minus the
+    eliminated blocks' Cholesky and coupling solves and the top Cholesky."""
+    elim = sum(chol + (1 + (1 if j + 1 < Nl else 0)) * n ** 3
+               for Nl in accounting.levels(N)[:-1] for j in range(1, Nl, 2)
+               for chol in [accounting.chol_flops(n)])
+    expect = accounting.cr_flops(N, n, 1)["factor"] - elim - accounting.chol_flops(n)
+    assert abs(accounting.tc_tile_flops(N, n) - expect) <= 1e-9 * max(expect, 1.0)

@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py (no GPU): the FP64 ALU peak, the parse of
 the committed ncu summary, the per-level split of the barrier stamps and the
 parse of the sampled clocks with their throttle reasons."""
+import json
 import os
 import tempfile
 
@@ -14,14 +15,23 @@ def test_fp64_alu_peak_from_unit_counts():
     assert bench.fp64_peak(152, 2070) == pytest.approx(1.259e12, rel=1e-3)
 
 
-def test_profiled_traffic_follows_the_committed_summary():
-    txt = open(bench.PROFILE).read()
-    per_block = float(txt.split("dram_bytes_per_block:")[1].split()[0])
+def test_profiled_traffic_follows_the_committed_capture():
+    rec = json.load(open(bench.TRAFFIC))
     got = bench.profiled_traffic(16384)
-    if "kernel_sources_sha256: " + bench.csrc_digest() in txt:
-        assert got == pytest.approx(per_block * 16384)
+    if rec["kernel_sources_sha256"] == bench.csrc_digest():
+        assert got == pytest.approx(rec["dram_bytes_per_block"] * 16384)
     else:  # the kernels changed since the capture: no traffic figure
         assert got is None
+
+
+def test_kernel_rooflines_from_class_times():
+    # residual: 6 n^2 d N flops per launch; two launches of 1 ms each
+    kt = {"residual": (2.0, 2), "correction": (4.0, 2), "solve": (0.0, 0)}
+    r = bench.kernel_rooflines(kt, N=100, n=8, d=2, mode="fp32_ir", sms=152, mhz=2070)
+    assert set(r) == {"residual", "correction"}
+    assert r["residual"]["achieved"] == pytest.approx(6 * 64 * 2 * 100 / 1e-3 / 1e12)
+    assert r["residual"]["frac"] == pytest.approx(r["residual"]["achieved"] / r["residual"]["peak"])
+    assert r["correction"]["bound"] == "hbm" and r["correction"]["unit"] == "GB/s"
 
 
 def test_phase_split_maps_stamps_to_levels():

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2509_03015_gb300 import inputs
+from tests._helpers import assert_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,6 +47,7 @@ def test_large_fp64_parity(oracle_mod, N, n, d):
     L, C = oracle_mod.factor(s["A_diag"], s["A_sub"])
     Xo = oracle_mod.solve(L, C, s["B"])
     assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+    assert_elementwise(X, Xo, rtol=1e-10, atol_frac=1e-12)
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
     ldo = oracle_mod.logdet(L)
     assert abs(ld - ldo) <= 1e-12 * max(1.0, abs(ldo))
@@ -88,15 +90,24 @@ def test_large_not_spd():
     solver.close()
 
 
-def test_kalman_N4096_n256_fp32_ir_full(oracle_mod):
+def test_kalman_N4096_n256_fp32_ir_full(oracle_mod, mixed_workload_oracle):
     """The mixed-precision workload at full size: FP32 factors, FP64
     residual refinement to backward error <= 1e-14; forward error against
     the FP64 oracle (kappa ~ 1e5 bounds it by ~kappa * u)."""
-    s = inputs.workload("kalman-N4096-n256-d16-rho0.99")
+    s, Xo = mixed_workload_oracle
     X, _, info = _solve(s, precision="fp32_ir")
     assert info.backward_err <= BWD_TOL
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
-    Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
     fe = oracle_mod.forward_error(X, Xo)
     print(f"N4096 n256: refine iters {info.iters}, backward {info.backward_err:.2e}, forward vs oracle {fe:.2e}")
     assert fe <= 1e-9
+    assert_elementwise(X, Xo, rtol=1e-7, atol_frac=1e-9)
+
+
+def test_kalman_N4096_n256_fp64_full(oracle_mod, mixed_workload_oracle):
+    """The same workload on the plain FP64 tiled path, against the oracle."""
+    s, Xo = mixed_workload_oracle
+    X, _, _ = _solve(s, precision="fp64")
+    assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+    assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
+    assert_elementwise(X, Xo, rtol=1e-7, atol_frac=1e-10)

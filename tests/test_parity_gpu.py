@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2509_03015_gb300 import inputs
+from tests._helpers import assert_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -65,6 +66,7 @@ def test_fp64_parity_random(oracle_mod, N, n, d):
     L, C = oracle_mod.factor(s["A_diag"], s["A_sub"])
     Xo = oracle_mod.solve(L, C, s["B"])
     assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+    assert_elementwise(X, Xo, rtol=1e-10, atol_frac=1e-12)
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
     ldo = oracle_mod.logdet(L)
     assert abs(ld - ldo) <= 1e-12 * max(1.0, abs(ldo))
@@ -104,6 +106,7 @@ def test_kalman_workloads_full(oracle_mod, name):
     L, C = oracle_mod.factor(s["A_diag"], s["A_sub"])
     Xo = oracle_mod.solve(L, C, s["B"])
     assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+    assert_elementwise(X, Xo, rtol=1e-9, atol_frac=1e-11)
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
     assert abs(ld - oracle_mod.logdet(L)) <= 1e-12 * abs(oracle_mod.logdet(L))
 
@@ -117,6 +120,7 @@ def test_kalman_N16384_n64_full(oracle_mod):
     L, C = oracle_mod.factor(s["A_diag"], s["A_sub"])
     Xo = oracle_mod.solve(L, C, s["B"])
     assert oracle_mod.forward_error(X, Xo) <= FWD_TOL
+    assert_elementwise(X, Xo, rtol=1e-9, atol_frac=1e-11)
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= BWD_TOL
     assert abs(ld - oracle_mod.logdet(L)) <= 1e-12 * abs(oracle_mod.logdet(L))
 

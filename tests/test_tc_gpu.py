@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2509_03015_gb300 import inputs
+from tests._helpers import assert_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,15 +39,22 @@ def test_tf32_ir_parity(oracle_mod, N, n, d):
     assert info.backward_err <= 1e-14
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= 1e-14
     assert oracle_mod.forward_error(X, Xo) <= 1e-10
+    assert_elementwise(X, Xo, rtol=1e-9, atol_frac=1e-11)
 
 
-def test_tf32_ir_kalman_N4096_n256(oracle_mod):
+def test_tf32_ir_kalman_N4096_n256(oracle_mod, mixed_workload_oracle):
+    """The mixed-precision workload at full size in TF32 mode: backward error
+    <= 1e-14 after refinement and the error against the FP64 oracle, bounded
+    by about kappa u_64 (kappa ~ 1e5) with room for the refinement's stop."""
     from paper_2509_03015_gb300 import Solver
-    s = inputs.workload("kalman-N4096-n256-d16-rho0.99")
+    s, Xo = mixed_workload_oracle
     solver = Solver(4096, 256, d_max=16, precision="tf32_ir")
     X = solver.factor_solve(_dev(s["A_diag"]), _dev(s["A_sub"]), _dev(s["B"])).cpu().numpy()
     info = solver.last_info
     solver.close()
     assert info.backward_err <= 1e-14
     assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= 1e-14
-    print(f"tf32_ir N4096 n256: iters {info.iters}, backward {info.backward_err:.2e}")
+    fe = oracle_mod.forward_error(X, Xo)
+    print(f"tf32_ir N4096 n256: iters {info.iters}, backward {info.backward_err:.2e}, forward vs oracle {fe:.2e}")
+    assert fe <= 1e-9
+    assert_elementwise(X, Xo, rtol=1e-7, atol_frac=1e-9)
