@@ -47,3 +47,44 @@ def test_tc_tile_flops_is_the_separator_part_of_cr(N, n):
                for chol in [accounting.chol_flops(n)])
     expect = accounting.cr_flops(N, n, 1)["factor"] - elim - accounting.chol_flops(n)
     assert abs(accounting.tc_tile_flops(N, n) - expect) <= 1e-9 * max(expect, 1.0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 8, 9, 33, 100, 1000, 16384])
+@pytest.mark.parametrize("n,d", [(1, 1), (4, 2), (64, 4)])
+def test_segment_flops_J1_is_cyclic_reduction(N, n, d):
+    """Segments of one block with separators at the even positions are the
+    odd-even cyclic reduction the kernels run: the two tallies agree."""
+    a = accounting.segment_flops(N, n, d, J=1)
+    b = accounting.cr_flops(N, n, d)
+    assert a["factor"] == pytest.approx(b["factor"], rel=1e-12)
+    assert a["solve"] == pytest.approx(b["solve"], rel=1e-12)
+
+
+@pytest.mark.parametrize("N,n,d", [(1, 3, 1), (7, 5, 2), (100, 8, 1), (16384, 64, 4)])
+def test_segment_flops_serial_crossover_is_block_thomas(N, n, d):
+    """N <= N_*: no recursion, the serial sweep of Algorithm 1 with K = 1."""
+    assert accounting.segment_flops(N, n, d, J=3, n_star=N) == accounting.thomas_flops(N, n, d)
+
+
+@pytest.mark.parametrize("J", [1, 2, 3, 7, 15, 63])
+def test_segments_do_not_cut_the_arithmetic(J):
+    """The paper's segment form does not lower the flops of cyclic reduction:
+    eliminating an interior block of a segment costs chol + 6 n^3 (its sweep,
+    the fill of the left coupling, the separator update) exactly as one CR
+    elimination does.  Over all levels N - 1 blocks are eliminated either way,
+    so for large N both tallies approach (N - 1)(n^3/3 + 6 n^3) and exceed the
+    block-Thomas tally by about (6 + 1/3) / (2 + 1/3) = 2.7x."""
+    N, n, d = 16384, 64, 4
+    seg = accounting.segment_flops(N, n, d, J)["factor"]
+    cr = accounting.cr_flops(N, n, d)["factor"]
+    th = accounting.thomas_flops(N, n, d)["factor"]
+    per_block = (N - 1) * (n ** 3 / 3 + 6 * n ** 3)
+    assert abs(seg - per_block) / per_block < 0.02
+    assert abs(seg - cr) / cr < 0.02
+    assert 2.6 < seg / th < 2.75
+
+
+def test_segment_levels():
+    assert accounting.segment_levels(9, 3) == [9, 3, 1]
+    assert accounting.segment_levels(9, 1) == accounting.levels(9)
+    assert accounting.segment_levels(100, 1, n_star=16) == [100, 50, 25, 13]
