@@ -91,12 +91,24 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def kernel_rooflines(kt, N, n, d, mode, sms, mhz):
+def emu_bytes(N, n, d):
+    """Bytes of the tensor-core residual per call: the operator's BF16 digit
+    slices (10 per entry of the 3n-wide operator rows, blocks padded to a
+    multiple of 64), X's slices (16 columns), and B, X in and R out."""
+    np_ = -(-n // 64) * 64
+    return N * 10 * n * 3 * np_ * 2 + N * 10 * 16 * np_ * 2 + 8.0 * N * n * d * 2 + 4.0 * N * n * d
+
+
+def kernel_rooflines(kt, steps, units, N, n, d, mode, sms, mhz, emu=False):
     """Roofline of each kernel class of one mixed-precision (or FP64) step from
-    its CUDA-event times: kt = {class: (ms, launches)} summed over the timed
-    steps.  Work per launch (algorithmic):
+    its CUDA-event times: kt = {class: (ms, launches)} summed over `steps`
+    timed steps; units[class] = work units of the class per step (residuals,
+    corrections; one factorisation).  Work per unit (algorithmic):
       residual    6 n^2 d N flops (three n x n blocks times d columns per block
-                  row), FP64 ALU;
+                  row), FP64 ALU; on the tensor cores (emu) the digit slices
+                  streamed from HBM (emu_bytes);
+      slice       the operator sliced once per factorisation: A read
+                  (2 N n^2 doubles) and the slices written, HBM;
       correction  the stored factors streamed up and down once each:
                   2 x 4 B x (N + slots) n^2, plus X (FP64, read + write) and the
                   FP32 residual: HBM;
@@ -111,12 +123,20 @@ def kernel_rooflines(kt, N, n, d, mode, sms, mhz):
     slots = sum(Nl - 1 for Nl in accounting.levels(N)[:-1])
     esz = 8 if mode == "fp64" else 4
     for cls, (ms, launches) in kt.items():
-        if launches <= 0 or ms <= 0:
+        u = units.get(cls, 0)
+        if launches <= 0 or ms <= 0 or u <= 0:
             continue
-        per = ms / launches * 1e-3
-        if cls == "residual":
+        per = ms / steps / u * 1e-3  # seconds per work unit
+        if cls == "residual" and emu:
+            work, unit, bound = emu_bytes(N, n, d), "GB/s", "hbm"
+            peak, pdef = pk["hbm_gbs"] * 1e9, f"HBM copy bandwidth ({pk['source']}); digit slices streamed"
+        elif cls == "residual":
             work, unit, bound = 6.0 * n * n * d * N, "TFLOP/s", "alu"
             peak, pdef = fp64_peak(sms, mhz), "FP64 ALU (SMs x 2 DFMA/clk x 2 x clock)"
+        elif cls == "slice":
+            np_ = -(-n // 64) * 64
+            work, unit, bound = 16.0 * N * n * n + 20.0 * N * n * 3 * np_, "GB/s", "hbm"
+            peak, pdef = pk["hbm_gbs"] * 1e9, f"HBM copy bandwidth ({pk['source']})"
         elif cls == "correction":
             work = 2.0 * esz * (N + slots) * n * n + 8.0 * N * n * d * 2 + 4.0 * N * n * d
             unit, bound = "GB/s", "hbm"
@@ -135,8 +155,8 @@ def kernel_rooflines(kt, N, n, d, mode, sms, mhz):
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         ach = work / per
         out[cls] = {"bound": bound, "achieved": ach / scale, "peak": peak / scale, "unit": unit,
-                    "frac": ach / peak, "launch_ms": per * 1e3, "launches": launches,
-                    "work_per_launch": work, "peak_definition": pdef}
+                    "frac": ach / peak, "ms_per_unit": per * 1e3, "units_per_step": u,
+                    "launches_per_step": launches / steps, "work_per_unit": work, "peak_definition": pdef}
         if cls == "schur_tc":
             out[cls]["executed_frac"] = 3 * ach / peak
     return out
@@ -287,16 +307,26 @@ def timed_leg(sol, call, reps, stream, max_over_ranks, N, n, d, mode, sms, mhz):
     the per-class times and their rooflines."""
     sol.set_option("kernel_timing", 1)
     kt = {}
+    refs = [0, 0]
 
     def step():
         call()
         for c, (ms, k) in sol.kernel_times().items():
             a = kt.get(c, (0.0, 0))
             kt[c] = (a[0] + ms, a[1] + k)
+        if mode != "fp64":
+            plain, cg = sol.refine_stats()
+            refs[0] += plain
+            refs[1] += cg
     ms = _timed(step, reps, stream, max_over_ranks)
     sol.set_option("kernel_timing", 0)
     per_step = {c: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for c, v in kt.items() if v[1]}
-    roof = kernel_rooflines(kt, N, n, d, mode, sms, mhz)
+    # work units per step: one factorisation; each residual is one launch;
+    # each plain refinement step is one correction
+    units = {"factor": 1, "schur_tc": 1, "residual": kt.get("residual", (0, 0))[1] / reps,
+             "correction": refs[0] / reps, "slice": kt.get("slice", (0, 0))[1] / reps}
+    emu = mode != "fp64" and 64 < n <= 256 and d <= 16
+    roof = kernel_rooflines(kt, reps, units, N, n, d, mode, sms, mhz, emu=emu)
     dom = max(per_step, key=lambda c: per_step[c]["ms_per_step"]) if per_step else None
     return ms, per_step, roof, dom
 

@@ -117,6 +117,11 @@ typedef enum {
                                    first use; at most 4 cycles, each restarted from the
                                    true FP64 residual */
   BDSS_OPT_MAX_KRYLOV_ITERS = 8, /* mixed precision: CG iterations per cycle (default 300) */
+  BDSS_OPT_RESIDUAL_EMU = 10,   /* mixed precision, 64 < n <= 256 and d_max <= 16: 1 (default)
+                                   = the FP64 residual of the refinement on the tensor cores
+                                   (BF16 digit slices, exact FP32 accumulation: see
+                                   bdss_residual); 0 = on the FP64 ALU.  Setting 1 on a
+                                   handle without it gives BDSS_ERR_UNSUPPORTED */
   BDSS_OPT_KERNEL_TIMING = 9    /* 1: time every launch (group) of each following call with
                                    CUDA events recorded on the handle's stream, by kernel
                                    class (bdss_kernel_class); read with
@@ -132,7 +137,8 @@ typedef enum {
   BDSS_KT_CORRECTION = 3,  /* mixed precision: refinement corrections X += M^-1 (B - A X) */
   BDSS_KT_RESIDUAL = 4,    /* mixed precision: FP64 residuals B - A X (with the backward-error norms) */
   BDSS_KT_KRYLOV = 5,      /* mixed precision: CG refinement kernels and their preconditioner solves */
-  BDSS_KT_CLASSES = 6
+  BDSS_KT_SLICE = 6,       /* mixed precision: slicing the operator for the tensor-core residual */
+  BDSS_KT_CLASSES = 7
 } bdss_kernel_class;
 
 /*
@@ -265,6 +271,25 @@ bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity
  * of the same FP32 inputs.  *max_rel_err = max |C_tc - C_ref| / sum_k |a b|
  * (host pointer).  Allocates and frees its own small buffers. */
 bdss_status bdss_tc_selftest(double *max_rel_err);
+
+/*
+ * R = B - A X for the A of the handle's last bdss_factor (or
+ * bdss_factor_solve), 1 <= d <= d_max; B, X readable by the device, R device
+ * memory, all N x n x d FP64.  The residual of the mixed-precision
+ * refinement, exposed: with BDSS_OPT_RESIDUAL_EMU on (mixed
+ * precision, 64 < n <= 256, d <= 16) it runs on the tensor cores -- every
+ * operator row [A_{i,i-1}, sym(A_ii), A_{i,i+1}] and every column of X is
+ * rounded to 59 bits below its maximum and cut into ten signed 6-bit digits
+ * (exact in BF16); all digit products are summed exactly in the FP32
+ * accumulators (no partial sum reaches 2^24) and combined in 64-bit integers
+ * and FP64, so |R - R_exact| stays within a few units of 2^-59 times the row
+ * maximum of A times the column maximum of X per term, FP64's own accuracy
+ * for the backward error ||B - A X|| / (||A|| ||X||).  The operator is sliced
+ * once per factorisation (about 30 n^2 bytes per block).  Otherwise R is
+ * formed on the FP64 ALU.  Not in the paper, which takes residuals of its
+ * final solutions only (Sec. 4); it is the residual of the refinement loop.
+ */
+bdss_status bdss_residual(bdss_handle h, const double *B, const double *X, int32_t d, double *R);
 
 /* Device time of the handle's last bdss_factor, bdss_solve or
  * bdss_factor_solve by kernel class, with BDSS_OPT_KERNEL_TIMING on: ms[c]

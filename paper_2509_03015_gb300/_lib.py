@@ -18,8 +18,8 @@ STATUS_NAMES = {
 PRECISIONS = {"fp64": 0, "fp32_ir": 1, "tf32_ir": 2}
 OPTIONS = {"timeout_ms": 0, "persistent": 1, "max_refine": 2, "target_berr_e18": 3, "debug_skip_arrive": 4,
            "debug_guards": 5, "debug_corrupt_guard": 6, "refine_krylov": 7, "max_krylov_iters": 8,
-           "kernel_timing": 9}
-KERNEL_CLASSES = ("factor", "schur_tc", "solve", "correction", "residual", "krylov")
+           "kernel_timing": 9, "residual_emu": 10}
+KERNEL_CLASSES = ("factor", "schur_tc", "solve", "correction", "residual", "krylov", "slice")
 
 
 class bdss_info(ctypes.Structure):
@@ -47,6 +47,7 @@ SIGNATURES = {
     "bdss_status_string": (ctypes.c_char_p, [_i32]),
     "bdss_last_cuda_error": (ctypes.c_char_p, []),
     "bdss_last_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
+    "bdss_residual": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "bdss_tc_selftest": (_i32, [ctypes.POINTER(ctypes.c_double)]),
     "bdss_adjoint_grads": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
     "bdss_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i32), _i32, _vp]),

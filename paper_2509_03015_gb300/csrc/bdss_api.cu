@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/bdss.h"
+#include "bdss_emu.h"
 #include "bdss_launch.h"
 #include "bdss_kalman.h"
 #include "bdss_krylov.h"
@@ -38,6 +39,8 @@ struct bdss_ctx {
   int tf32 = 0;         // TF32 mode on the large path: tensor-core Schur tiles
   CUtensorMap *d_tmap = nullptr;  // TMA map of Wb (device copy)
   double *Ltop = nullptr;
+  void *Li = nullptr;    // large mixed path: L^{-1} of the eliminated blocks (N n n, FP32)
+  float *Yt = nullptr;   // large mixed path: y of the eliminated blocks in solve passes (N n d_max)
   float *Y32 = nullptr;  // mixed: working RHS / correction (N n d_max)
   float *R32 = nullptr;  // mixed: FP32 residual (N n d_max)
   double *partial = nullptr;  // log-det partial sums
@@ -61,6 +64,13 @@ struct bdss_ctx {
   double *kr_R = nullptr, *kr_Z = nullptr, *kr_P = nullptr, *kr_Q = nullptr;
   double *kr_part = nullptr, *kr_sc = nullptr;
   int last_plain = 0, last_cg = 0;  // refinement steps of the last solve
+  // mixed precision, tiled path: the FP64-accurate residual on the tensor
+  // cores (sliced operator built once per factorisation)
+  EmuBuffers emu{};
+  CUtensorMap emu_maps[2];
+  int emu_ready = 0;     // buffers allocated and maps encoded
+  int emu_on = 0;        // option: use them
+  bool emu_sliced = false;
   int skip_barrier = 0;
   // stats of the last call
   int64_t launches = 0;
@@ -240,6 +250,7 @@ static Args<T> base_args(bdss_ctx *h) {
   a.capacity = h->bps * h->sms;
   a.tf32 = h->tf32;
   a.tmap_w = h->d_tmap;
+  a.Li = (T *)h->Li;
   return a;
 }
 
@@ -254,30 +265,33 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   // Schur-update tiles use that kernel and the Cholesky / substitution tasks
   // keep the two-CTA FP32 kernel.
   const bool tc_factor = sizeof(T) == 4 && h->tf32 && factor;
+  const int inv = a.Li ? 1 : 0;
+  Args<T> b = a;
+  if (!rhs) b.d = 0;
+  // solve passes with the stored inverses keep y of the eliminated blocks in Yt
+  b.Yt = (!factor && inv) ? (T *)h->Yt : nullptr;
   if (h->persistent && !tc_factor) {
     long long most = 1;
     for (int l = 0; l < p.L; ++l)
       for (int sub = 0; sub < 4; ++sub) {
-        const long long t = large_sub_tasks(p, l, sub, factor ? 1 : 0, rhs ? a.d : 0, esz, h->tf32);
+        const long long t = large_sub_tasks(p, l, sub, factor ? 1 : 0, rhs ? a.d : 0, esz, h->tf32, inv);
         if (t > most) most = t;
       }
     h->launches += 1;
     h->barriers += 1 + (factor ? 3 : 2) * p.L + ((rhs && p.L > 0) ? p.L : 0);
     kt_begin(h, h->kt_cls);
-    const cudaError_t e = launch_large_persistent<T>(a, factor ? 1 : 0, rhs ? 1 : 0, grid_for(h, most), h->smem,
+    const cudaError_t e = launch_large_persistent<T>(b, factor ? 1 : 0, rhs ? 1 : 0, grid_for(h, most), h->smem,
                                                      h->stream);
     kt_end(h, 1);
     return e;
   }
-  Args<T> b = a;
-  if (!rhs) b.d = 0;
   const int f = factor ? 1 : 0;
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < p.L && e == cudaSuccess; ++l)
     for (int sub = factor ? 0 : 1; sub < 3 && e == cudaSuccess; ++sub) {
       kt_begin(h, (tc_factor && sub == 2) ? BDSS_KT_SCHUR_TC : h->kt_cls);
-      e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz, h->tf32)), h->smem,
-                              h->stream);
+      e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz, h->tf32, inv)),
+                              h->smem, h->stream);
       kt_end(h, 1);
       h->launches += 1;
     }
@@ -288,7 +302,8 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   if (rhs)
     for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
       kt_begin(h, h->kt_cls);
-      e = launch_large_sub<T>(b, l, 3, 0, grid_for(h, large_sub_tasks(p, l, 3, 0, b.d, esz, 0)), h->smem, h->stream);
+      e = launch_large_sub<T>(b, l, 3, 0, grid_for(h, large_sub_tasks(p, l, 3, 0, b.d, esz, 0, inv)), h->smem,
+                              h->stream);
       kt_end(h, 1);
       h->launches += 1;
     }
@@ -367,6 +382,13 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->Eb);
   cudaFree(h->d_tmap);
   cudaFree(h->Ltop);
+  cudaFree(h->emu.Aslc);
+  cudaFree(h->emu.Aexp);
+  cudaFree(h->emu.Xslc);
+  cudaFree(h->emu.xexp);
+  cudaFree(h->emu.xmax);
+  cudaFree(h->Li);
+  cudaFree(h->Yt);
   cudaFree(h->Y32);
   cudaFree(h->R32);
   cudaFree(h->partial);
@@ -446,6 +468,28 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
     const size_t nd = (size_t)N * n * d_max;
     ok = ws_alloc(h, (void **)&h->Y32, nd * sizeof(float));
     ok = ok && ws_alloc(h, (void **)&h->R32, nd * sizeof(float));
+    if (h->large) {  // inverse factors and the y buffer of the solve passes
+      ok = ok && ws_alloc(h, &h->Li, (size_t)N * nn * sizeof(float));
+      ok = ok && ws_alloc(h, (void **)&h->Yt, nd * sizeof(float));
+    }
+    if (ok && h->large && d_max <= kEmuDp) {  // the tensor-core FP64 residual
+      ok = ws_alloc(h, (void **)&h->emu.Aslc, emu_aslc_bytes(N, n));
+      ok = ok && ws_alloc(h, (void **)&h->emu.Aexp, (size_t)N * n * sizeof(int));
+      ok = ok && ws_alloc(h, (void **)&h->emu.Xslc, emu_xslc_bytes(N, n));
+      ok = ok && ws_alloc(h, (void **)&h->emu.xexp, kEmuDp * sizeof(int));
+      ok = ok && ws_alloc(h, (void **)&h->emu.xmax, kEmuDp * sizeof(unsigned long long));
+      if (ok) {
+        h->emu.maps = h->emu_maps;
+        const cudaError_t em = emu_make_maps(h->emu, N, n);
+        const cudaError_t ec = em == cudaSuccess ? emu_configure() : em;
+        if (ec != cudaSuccess) {
+          bdss_destroy(h);
+          return cuda_fail(ec);
+        }
+        h->emu_ready = 1;
+        h->emu_on = 1;
+      }
+    }
   }
   if (!ok) {
     cudaGetLastError();  // clear the allocation error
@@ -491,6 +535,12 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
     case BDSS_OPT_MAX_KRYLOV_ITERS:
       if (value < 1 || value > 100000) return BDSS_ERR_INVALID_ARG;
       h->max_krylov = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_RESIDUAL_EMU:
+      if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
+      if (value && !h->emu_ready) return BDSS_ERR_UNSUPPORTED;
+      h->emu_on = (int)value;
+      h->norm_valid = false;  // the two residual paths form ||A||_inf alike, but afresh
       return BDSS_OK;
     case BDSS_OPT_KERNEL_TIMING:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
@@ -617,6 +667,7 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
   bdss_status st = finish(h, info);
   if (st != BDSS_OK) return st;
   h->norm_valid = false;  // ||A||_inf comes with the first residual
+  h->emu_sliced = false;  // the sliced operator is rebuilt from the new A
   h->A_diag = A_diag;
   h->A_sub = A_sub;
   h->factored = true;
@@ -627,11 +678,35 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
 // Backward error ||B - A X||_inf / (||A||_inf ||X||_inf) of the current X from
 // the FP64 residual kernel, which also leaves the residual in R32 (FP32) for a
 // plain correction and forms ||A||_inf on its first call.
+// Slice the operator for the tensor-core residual if this factorisation has
+// not been sliced yet; forms ||A||_inf into the status word (reset before).
+static cudaError_t emu_slice_if_needed(bdss_ctx *h) {
+  if (h->emu_sliced) return cudaSuccess;
+  kt_begin(h, BDSS_KT_SLICE);
+  const cudaError_t e = launch_emu_slice_operator(h->N, h->n, h->A_diag, h->A_sub, h->emu, h->dst, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  if (e == cudaSuccess) h->emu_sliced = true;
+  return e;
+}
+
+static bool use_emu(const bdss_ctx *h, int d) { return h->emu_on && d <= kEmuDp; }
+
 static bdss_status residual_berr(bdss_ctx *h, const double *B, const double *X, int d, double *berr) {
   cudaError_t e = reset_status(h);
-  const int with_norm = h->norm_valid ? 0 : 1;
+  const bool emu = use_emu(h, d);
+  int with_norm = h->norm_valid ? 0 : 1;
+  if (emu && (!h->emu_sliced || !h->norm_valid)) {
+    h->emu_sliced = false;
+    if (e == cudaSuccess) e = emu_slice_if_needed(h);  // its ||A||_inf lands in nrm[2]
+    with_norm = 1;
+  } else if (emu) {
+    with_norm = 0;
+  }
   kt_begin(h, BDSS_KT_RESIDUAL);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && emu)
+    e = launch_emu_residual(h->N, h->n, d, X, B, h->R32, nullptr, h->emu, h->dst, h->timeout_ns, h->sms, h->stream);
+  else if (e == cudaSuccess)
     e = h->large ? launch_residual_rows(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
                                         (int)std::min<long long>(h->N, 2LL * h->sms), h->stream)
                  : launch_residual(h->N, h->n, d, h->A_diag, h->A_sub, X, B, h->R32, h->dst, with_norm,
@@ -967,6 +1042,24 @@ bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity
   for (int i = 0; i < c; ++i) release_ns[i] = h->trace[i];
   if (count) *count = h->trace_count;
   return BDSS_OK;
+}
+
+bdss_status bdss_residual(bdss_handle h, const double *B, const double *X, int32_t d, double *R) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  if (!B || !X || !R || !aligned16(B) || !aligned16(X) || !aligned16(R)) return BDSS_ERR_INVALID_ARG;
+  if (d < 1 || d > h->d_max) return BDSS_ERR_INVALID_ARG;
+  if (!device_readable(B) || !device_readable(X) || !device_memory(R)) return BDSS_ERR_INVALID_ARG;
+  if (!h->factored) return BDSS_ERR_NOT_FACTORED;
+  cudaError_t e = reset_status(h);
+  if (use_emu(h, d)) {
+    if (e == cudaSuccess) e = emu_slice_if_needed(h);
+    if (e == cudaSuccess)
+      e = launch_emu_residual(h->N, h->n, d, X, B, nullptr, R, h->emu, h->dst, h->timeout_ns, h->sms, h->stream);
+  } else if (e == cudaSuccess) {
+    e = launch_btd_apply(h->N, h->n, d, h->A_diag, h->A_sub, X, B, R, h->sms, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  return finish(h, nullptr);
 }
 
 bdss_status bdss_last_kernel_times(bdss_handle h, double *ms, int64_t *launches, int32_t classes) {

@@ -86,6 +86,12 @@ struct Args {
   int capacity;          // CTAs of a full persistent grid (tail-level splits)
   int tf32;              // large FP32 path: Schur products on tcgen05 (3xTF32)
   const CUtensorMap *tmap_w;  // TMA map of Wb as (slots * n) rows x n FP32 columns
+  T *Li;                 // large FP32 path: L^{-1} of every eliminated block (slot of
+                         // its original index, row-major n x n, zero above the
+                         // diagonal), formed by the factorisation; null elsewhere
+  T *Yt;                 // large FP32 path, solve passes: y_j = L_j^{-1} b_j of the
+                         // eliminated blocks (N x n x d), kept apart from Y because
+                         // row tiles of one block are formed by several CTAs
 };
 
 // Odd row stride of a staged n x n block (shared-memory bank spread).

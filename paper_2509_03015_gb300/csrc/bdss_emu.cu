@@ -1,0 +1,602 @@
+// FP64-accurate residual R = B - A X of the mixed-precision refinement on the
+// tcgen05 tensor cores, for the tiled path (64 < n <= 256, d <= 16).
+//
+// Representation.  An operator row (block row i, row r) is the 3n entries
+// [A_{i,i-1}[r][:], sym(A_ii)[r][:], A_{i+1,i}[:][r]] with one exponent E
+// (max |a| < 2^E).  Each entry becomes the 59-bit integer q = round(a 2^(59-E))
+// written as ten signed base-64 digits, q = sum_p d_p 64^(9-p) with
+// d_p in [-32, 32]; every digit is exact in BF16.  A column c of X gets one
+// exponent F over all blocks and the same cut.  Then
+//   sum_k a_k x_k = 2^(E+F-118) sum_t 64^(18-t) ACC_t,
+//   ACC_t = sum_{p+q=t} sum_k d_p(a_k) d_q(x_k),
+// where at most ten pairs meet on a diagonal t and K <= 3 x 256, so
+// |ACC_t| <= 10 x 768 x 32 x 32 < 2^23: every partial sum is an integer below
+// 2^24 and the FP32 accumulation of the tensor cores is exact whatever its
+// order.  The 19 diagonal sums are combined in 64-bit integers and FP64.  The
+// only error is the truncation of a and x to 59 bits below the row / column
+// maximum, so the residual is as accurate as an FP64 product in the normwise
+// sense of the backward error ||B - A X|| / (||A|| ||X||).
+//
+// Products.  One tcgen05.mma (kind::f16, BF16 in, FP32 accumulate) per A
+// slice p and K step of 16 covers all ten X slices at once: the B operand
+// stacks X's slices q = 0..9 (16 rows each, N = 160), and the D columns start
+// at 16 p, so the result for slice pair (p, q) lands on TMEM columns
+// 16 (p + q) .. + 15, the accumulator of diagonal p + q (304 columns).
+//
+// Kernel roles (one persistent CTA per SM, 192 threads): warp 0 issues the
+// TMA loads of the slices into a ring of shared-memory stages, warp 1 issues
+// the MMAs, warps 2-5 read the accumulators (one TMEM lane quarter each),
+// form R and the norms, and clear the accumulators for the next tile.  Every
+// wait is bounded; a timed-out wait sets BDSS_ERR_TIMEOUT, the roles stop,
+// loads and MMAs still in flight are waited out (bounded) and TMEM is freed.
+#include "bdss_emu.h"
+#include "bdss_tc.cuh"
+
+namespace bdss {
+
+namespace {
+
+constexpr int kS = kEmuSlices;
+constexpr int kFrac = 59;                 // fraction bits of the fixed-point digits
+constexpr int kDiag = 2 * kS - 1;         // accumulators (diagonals p + q)
+constexpr int kM = 128;                   // output rows of a tile (TMEM lanes)
+constexpr int kN = kS * kEmuDp;           // 160: X slices stacked as the B operand
+constexpr int kRowsPerCta = 16;           // operator rows per slicing CTA
+constexpr int kAStages = 8;
+constexpr int kXStages = 2;
+constexpr int kATile = kM * kEmuKc * 2;   // 16384 bytes
+constexpr int kXTile = kN * kEmuKc * 2;   // 20480 bytes
+constexpr int kEmuThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr size_t kResidualSmem = (size_t)kAStages * kATile + (size_t)kXStages * kXTile + 1024;
+
+// q = round(v 2^(59 - E)) from the bit fields of v (integer operations only;
+// |v| < 2^E gives |q| < 2^59).  Zero and subnormal inputs give 0.
+__device__ __forceinline__ long long emu_fixed(double v, int E) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) return 0;
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int sh = ex - 1075 + kFrac - E;
+  long long q;
+  if (sh >= 0) q = m << (sh > 6 ? 6 : sh);
+  else if (sh > -63) q = (m + (1LL << (-sh - 1))) >> (-sh);
+  else q = 0;
+  return b < 0 ? -q : q;
+}
+
+// Signed base-64 digits of q (|q| < 2^59): q = sum_p d[p] 64^(9-p),
+// d[p] in [-32, 31] for p >= 1 and |d[0]| <= 32.
+__device__ __forceinline__ void emu_digits(long long q, int (&d)[kS]) {
+#pragma unroll
+  for (int p = kS - 1; p > 0; --p) {
+    const int r = (int)((q + 32) & 63) - 32;
+    d[p] = r;
+    q = (q - r) >> 6;
+  }
+  d[0] = (int)q;
+}
+
+// BF16 bits of a small integer (|d| <= 64): 2^23 + d + 64 is exact in FP32,
+// subtracting 2^23 + 64 leaves d exactly, and d needs at most 7 significant
+// bits, so the upper half of its FP32 pattern is its BF16 pattern.
+__device__ __forceinline__ unsigned short emu_bf16(int d) {
+  const float f = __int_as_float(0x4B000000 + d + 64) - 8388672.0f;
+  return (unsigned short)(__float_as_uint(f) >> 16);
+}
+
+// Exponent E with max |x| < 2^E from the bits of max |x| (a zero maximum:
+// every digit is zero, any E works).
+__device__ __forceinline__ int emu_exp(unsigned long long maxbits) {
+  const int ex = (int)((maxbits >> 52) & 0x7FF);
+  return ex == 0 ? -1022 : ex - 1022;
+}
+
+// ---------------------------------------------------------------------------
+// Operator slices: CTA (block row i, rows r0 .. r0 + 15).
+// Aslc[((i S + p) n + r) 3np + g np + k] = digit p of entry k of block g of
+// operator row (i, r); g = 0: A_{i,i-1}, 1: sym(A_ii), 2: A_{i,i+1} =
+// A_{i+1,i}^T; zero for absent blocks and k >= n.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_emu_slice_operator(long long N, int n, int np, const double *A_diag,
+                                                            const double *A_sub, unsigned short *Aslc, int *Aexp,
+                                                            DevStatus *st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *T = reinterpret_cast<double *>(smem_raw);  // [3][kRowsPerCta][n]
+  __shared__ int sE[kRowsPerCta];
+  __shared__ float sNorm[8];
+  const int groups = (n + kRowsPerCta - 1) / kRowsPerCta;
+  const long long i = blockIdx.x / groups;
+  const int r0 = (int)(blockIdx.x % groups) * kRowsPerCta;
+  const int R = min(kRowsPerCta, n - r0);
+  const size_t nn = (size_t)n * n;
+  const bool hasL = i > 0, hasR = i + 1 < N;
+  double *T0 = T, *T1 = T + (size_t)kRowsPerCta * n, *T2 = T + (size_t)2 * kRowsPerCta * n;
+  // rows of A_{i,i-1} and A_ii
+  for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
+    const int rr = e / n, k = e - rr * n;
+    T0[e] = hasL ? __ldg(A_sub + (size_t)(i - 1) * nn + (size_t)(r0 + rr) * n + k) : 0.0;
+    T1[e] = __ldg(A_diag + (size_t)i * nn + (size_t)(r0 + rr) * n + k);
+  }
+  __syncthreads();
+  // columns r0 .. r0 + R - 1 of A_ii (symmetrise) and of A_{i+1,i}
+  for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
+    const int k = e / R, rr = e - k * R;
+    const double at = __ldg(A_diag + (size_t)i * nn + (size_t)k * n + r0 + rr);
+    T1[rr * n + k] = 0.5 * (T1[rr * n + k] + at);
+    T2[rr * n + k] = hasR ? __ldg(A_sub + (size_t)i * nn + (size_t)k * n + r0 + rr) : 0.0;
+  }
+  __syncthreads();
+  // row exponents and ||A||_inf row sums (FP32 from the bit fields)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float best = 0.0f;
+  for (int rr = warp; rr < R; rr += 8) {
+    unsigned long long mx = 0;
+    float sum = 0.0f;
+    for (int g = 0; g < 3; ++g)
+      for (int k = lane; k < n; k += 32) {
+        const double v = T[(size_t)g * kRowsPerCta * n + (size_t)rr * n + k];
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+        mx = b > mx ? b : mx;
+        sum += abs_f32_bits(v);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = m2 > mx ? m2 : mx;
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (lane == 0) {
+      sE[rr] = emu_exp(mx);
+      Aexp[(size_t)i * n + r0 + rr] = emu_exp(mx);
+    }
+    best = fmaxf(best, sum);
+  }
+  if (lane == 0) sNorm[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0 && st) {
+    float m = 0.0f;
+    for (int w = 0; w < 8; ++w) m = fmaxf(m, sNorm[w]);
+    atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong((double)m));
+  }
+  // digits: consecutive threads take consecutive k of one (row, block)
+  const int K3 = 3 * np;
+  for (int e = threadIdx.x; e < R * K3; e += blockDim.x) {
+    const int rr = e / K3, kk = e - rr * K3, g = kk / np, k = kk - g * np;
+    const double v = k < n ? T[(size_t)g * kRowsPerCta * n + (size_t)rr * n + k] : 0.0;
+    int dg[kS];
+    emu_digits(emu_fixed(v, sE[rr]), dg);
+#pragma unroll
+    for (int p = 0; p < kS; ++p)
+      Aslc[(((size_t)i * kS + p) * n + r0 + rr) * K3 + kk] = emu_bf16(dg[p]);
+  }
+}
+
+// max |X[:, c]| as FP64 bit patterns (xmax zeroed by the caller).
+__global__ void __launch_bounds__(256) k_emu_xmax(long long rows, int d, const double *X, unsigned long long *xmax) {
+  __shared__ unsigned long long sm[256];
+  const int c = threadIdx.x % kEmuDp, rg = threadIdx.x / kEmuDp;
+  unsigned long long mx = 0;
+  if (c < d)
+    for (long long r = (long long)blockIdx.x * 16 + rg; r < rows; r += (long long)gridDim.x * 16) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(X + r * d + c)) & 0x7FFFFFFFFFFFFFFFULL;
+      mx = b > mx ? b : mx;
+    }
+  sm[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x < kEmuDp && threadIdx.x < d) {
+    unsigned long long m = 0;
+    for (int g = 0; g < 16; ++g) m = sm[g * kEmuDp + threadIdx.x] > m ? sm[g * kEmuDp + threadIdx.x] : m;
+    atomicMax(xmax + threadIdx.x, m);
+  }
+}
+
+// X slices, one CTA per block j: Xslc[((j S + q) 16 + c) np + k] = digit q of
+// X_j[k][c] with column exponent F_c; zero for c >= d or k >= n.
+__global__ void __launch_bounds__(256) k_emu_slice_x(long long N, int n, int np, int d, const double *X,
+                                                     const unsigned long long *xmax, int *xexp,
+                                                     unsigned short *Xslc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *sX = reinterpret_cast<double *>(smem_raw);  // n x d
+  __shared__ int sF[kEmuDp];
+  const long long j = blockIdx.x;
+  if (threadIdx.x < kEmuDp) {
+    sF[threadIdx.x] = threadIdx.x < d ? emu_exp(xmax[threadIdx.x]) : 0;
+    if (j == 0) xexp[threadIdx.x] = sF[threadIdx.x];
+  }
+  for (int e = threadIdx.x; e < n * d; e += blockDim.x) sX[e] = __ldg(X + (size_t)j * n * d + e);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kEmuDp * np; e += blockDim.x) {
+    const int c = e / np, k = e - c * np;
+    const double v = (c < d && k < n) ? sX[k * d + c] : 0.0;
+    int dg[kS];
+    emu_digits(emu_fixed(v, sF[c]), dg);
+#pragma unroll
+    for (int q = 0; q < kS; ++q) Xslc[(((size_t)j * kS + q) * kEmuDp + c) * np + k] = emu_bf16(dg[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The tensor-core residual.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool emu_try(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait (the limit counts from the first failed poll) that also gives
+// up when another role has aborted (abort != null; the drains at the end
+// pass null and wait for their loads and MMAs whatever happened).
+__device__ __forceinline__ bool emu_wait(uint64_t *bar, uint32_t parity, long long timeout_ns, volatile int *abort) {
+  long long ts = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (emu_try(bar, parity)) return true;
+    if ((it & 63) == 63) {
+      if (abort && *abort) return false;
+      const long long now = global_ns();
+      if (ts == 0) ts = now;
+      else if (now - ts > timeout_ns) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void emu_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void emu_mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc)
+      : "memory");
+}
+
+// D = FP32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t emu_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
+struct EmuKArgs {
+  long long N;
+  int n, np, d;
+  const int *Aexp, *xexp;
+  const double *X, *B;
+  float *R32;
+  double *R64;
+  DevStatus *st;
+  long long timeout_ns;
+};
+
+__global__ void __launch_bounds__(kEmuThreads, 1)
+    k_emu_residual(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX,
+                   const __grid_constant__ EmuKArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t a_full[kAStages], a_empty[kAStages], x_full[kXStages], x_empty[kXStages];
+  __shared__ uint64_t acc_full, acc_empty, drain;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int sF[kEmuDp];
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~(uintptr_t)1023);
+  unsigned char *Ast = base;                                  // kAStages x 16 KB
+  unsigned char *Xst = base + (size_t)kAStages * kATile;      // kXStages x 20 KB
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.n, np = a.np, d = a.d;
+  const long long N = a.N;
+  const int MT = (n + kM - 1) / kM, kchunks = np / kEmuKc;
+  const long long tiles = N * MT;
+  volatile int *abort = &s_abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kAStages; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < kXStages; ++s) {
+      mbar_init(&x_full[s], 1);
+      mbar_init(&x_empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 128);
+    mbar_init(&drain, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < kEmuDp) sF[threadIdx.x] = a.xexp[threadIdx.x];
+  if (warp == 1) tmem_alloc(&s_tmem, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  auto fail = [&]() {
+    *abort = 1;
+    set_status(a.st, kStTimeout, -1, -1);
+  };
+
+  if (warp == 0) {
+    // ---- TMA producer -------------------------------------------------------
+    if (lane == 0) {
+      int as = 0, xs = 0;
+      uint32_t aph = 0, xph = 0;
+      for (long long t = blockIdx.x; t < tiles && !*abort; t += gridDim.x) {
+        const long long i = t / MT;
+        const int m = (int)(t % MT);
+        for (int g = 0; g < 3 && !*abort; ++g) {
+          if ((g == 0 && i == 0) || (g == 2 && i == N - 1)) continue;
+          for (int kk = 0; kk < kchunks; ++kk) {
+            if (!emu_wait(&x_empty[xs], xph ^ 1, a.timeout_ns, abort)) { fail(); break; }
+            mbar_expect_tx(&x_full[xs], kXTile);
+            tma_load_2d(Xst + (size_t)xs * kXTile, &mapX, kk * kEmuKc, (int)((i - 1 + g) * kS * kEmuDp),
+                        &x_full[xs]);
+            if (++xs == kXStages) { xs = 0; xph ^= 1; }
+            for (int p = 0; p < kS; ++p) {
+              if (!emu_wait(&a_empty[as], aph ^ 1, a.timeout_ns, abort)) { fail(); break; }
+              mbar_expect_tx(&a_full[as], kATile);
+              tma_load_2d(Ast + (size_t)as * kATile, &mapA, g * np + kk * kEmuKc,
+                          (int)((i * kS + p) * n + m * kM), &a_full[as]);
+              if (++as == kAStages) { as = 0; aph ^= 1; }
+            }
+            if (*abort) break;
+          }
+        }
+      }
+      // wait out the loads still in flight (each stage's last armed phase)
+      for (int s = 0; s < kAStages; ++s) {
+        const uint32_t ph = (s < as) ? aph : (aph ^ 1);
+        emu_wait(&a_full[s], ph, a.timeout_ns, nullptr);
+      }
+      for (int s = 0; s < kXStages; ++s) {
+        const uint32_t ph = (s < xs) ? xph : (xph ^ 1);
+        emu_wait(&x_full[s], ph, a.timeout_ns, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ------------------------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = emu_idesc(kM, kN);
+      int as = 0, xs = 0;
+      uint32_t aph = 0, xph = 0, eph = 0;
+      for (long long t = blockIdx.x; t < tiles && !*abort; t += gridDim.x) {
+        const long long i = t / MT;
+        if (!emu_wait(&acc_empty, eph, a.timeout_ns, abort)) { fail(); break; }
+        eph ^= 1;
+        tc_fence_after();
+        for (int g = 0; g < 3 && !*abort; ++g) {
+          if ((g == 0 && i == 0) || (g == 2 && i == N - 1)) continue;
+          for (int kk = 0; kk < kchunks; ++kk) {
+            if (!emu_wait(&x_full[xs], xph, a.timeout_ns, abort)) { fail(); break; }
+            const unsigned char *xb = Xst + (size_t)xs * kXTile;
+            for (int p = 0; p < kS; ++p) {
+              if (!emu_wait(&a_full[as], aph, a.timeout_ns, abort)) { fail(); break; }
+              tc_fence_after();
+              const unsigned char *ab = Ast + (size_t)as * kATile;
+#pragma unroll
+              for (int ks = 0; ks < kEmuKc / 16; ++ks)
+                emu_mma_bf16(tmem + (uint32_t)(p * kEmuDp), tc_desc_sw128(ab, ks * 32), tc_desc_sw128(xb, ks * 32),
+                             idesc);
+              tc_commit(&a_empty[as]);
+              if (++as == kAStages) { as = 0; aph ^= 1; }
+            }
+            tc_commit(&x_empty[xs]);
+            if (++xs == kXStages) { xs = 0; xph ^= 1; }
+            if (*abort) break;
+          }
+        }
+        tc_commit(&acc_full);
+      }
+      // every MMA issued has completed before TMEM is released
+      tc_commit(&drain);
+      emu_wait(&drain, 0, a.timeout_ns, nullptr);
+    }
+  } else {
+    // ---- epilogue: warps 2..5, TMEM lane quarter warp % 4 ---------------------
+    const int quarter = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    const int row = 32 * quarter + lane;
+    auto clear = [&]() {
+      for (int t = 0; t < kDiag; ++t) tmem_zero16(lane_base + (uint32_t)(t * kEmuDp));
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      emu_arrive(&acc_empty);
+    };
+    clear();
+    uint32_t fph = 0;
+    double maxR = 0.0, maxX = 0.0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const long long i = t / MT;
+      const int m = (int)(t % MT);
+      // warp-uniform wait: lane 0 polls, the others then observe the phase
+      int ok = 0;
+      if (lane == 0) ok = emu_wait(&acc_full, fph, a.timeout_ns, abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
+      if (lane != 0) emu_try(&acc_full, fph);
+      fph ^= 1;
+      tc_fence_after();
+      // v[c] = sum_t 64^(18 - t) ACC_t[c], in three integer groups
+      double v[kEmuDp];
+      {
+        long long G[kEmuDp];
+#pragma unroll
+        for (int c = 0; c < kEmuDp; ++c) G[c] = 0;
+        for (int t = 0; t < kDiag; ++t) {
+          uint32_t r[16];
+          tmem_ld16(lane_base + (uint32_t)(t * kEmuDp), r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < kEmuDp; ++c) G[c] = G[c] * 64 + (long long)__float2int_rn(__uint_as_float(r[c]));
+          if (t == 6 || t == 13 || t == kDiag - 1) {
+            const double w = t == 6 ? 4722366482869645213696.0 /* 2^72 */ : t == 13 ? 1073741824.0 /* 2^30 */ : 1.0;
+#pragma unroll
+            for (int c = 0; c < kEmuDp; ++c) {
+              v[c] = (t == 6) ? (double)G[c] * w : fma((double)G[c], w, v[c]);
+              G[c] = 0;
+            }
+          }
+        }
+      }
+      const int r = m * kM + row;
+      if (r < n) {
+        const int Ea = a.Aexp[(size_t)i * n + r];
+        const size_t o = ((size_t)i * n + r) * d;
+        double rs = 0.0, xs = 0.0;
+#pragma unroll
+        for (int c = 0; c < kEmuDp; ++c) {
+          if (c < d) {
+            // an Inf or NaN in the operator row or in column c of X (its
+            // maximum's exponent field is all ones: E = 1025) poisons the entry,
+            // as an FP64 product would
+            const double ax = (Ea > 1024 || sF[c] > 1024) ? __longlong_as_double(0x7FF8000000000000LL)
+                                                          : scalbn(v[c], Ea + sF[c] - 2 * kFrac);
+            const double res = __ldg(a.B + o + c) - ax;
+            if (a.R32) a.R32[o + c] = (float)res;
+            if (a.R64) a.R64[o + c] = res;
+            rs += fabs(res);
+            xs += fabs(__ldg(a.X + o + c));
+          }
+        }
+        // a NaN anywhere (e.g. an FP32 solve that overflowed) must reach the
+        // host's backward-error test: keep it instead of fmax dropping it
+        maxR = (rs > maxR || rs != rs) ? rs : maxR;
+        maxX = (xs > maxX || xs != xs) ? xs : maxX;
+      }
+      tc_fence_before();
+      clear();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double r2 = __shfl_xor_sync(0xffffffffu, maxR, o), x2 = __shfl_xor_sync(0xffffffffu, maxX, o);
+      maxR = (r2 > maxR || r2 != r2) ? r2 : maxR;
+      maxX = (x2 > maxX || x2 != x2) ? x2 : maxX;
+    }
+    if (lane == 0) {
+      atomicMax(&a.st->nrm[0], (unsigned long long)__double_as_longlong(maxR));
+      atomicMax(&a.st->nrm[1], (unsigned long long)__double_as_longlong(maxX));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_bf16_2d(CUtensorMap *out, void *base, unsigned long long cols, unsigned long long rows,
+                           unsigned box_cols, unsigned box_rows) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = (EncodeTiledFn)p;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t emu_aslc_bytes(long long N, int n) { return (size_t)N * kS * n * 3 * emu_np(n) * 2; }
+size_t emu_xslc_bytes(long long N, int n) { return (size_t)N * kS * kEmuDp * emu_np(n) * 2; }
+
+cudaError_t emu_make_maps(EmuBuffers &b, long long N, int n) {
+  const int np = emu_np(n);
+  cudaError_t e = encode_bf16_2d(&b.maps[0], b.Aslc, (unsigned long long)3 * np, (unsigned long long)N * kS * n,
+                                 kEmuKc, kM);
+  if (e == cudaSuccess)
+    e = encode_bf16_2d(&b.maps[1], b.Xslc, (unsigned long long)np, (unsigned long long)N * kS * kEmuDp, kEmuKc, kN);
+  return e;
+}
+
+cudaError_t emu_configure() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const void *kernels[] = {(const void *)k_emu_residual, (const void *)k_emu_slice_operator,
+                           (const void *)k_emu_slice_x};
+  for (const void *k : kernels) {
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  }
+  if (e == cudaSuccess && kResidualSmem > (size_t)optin) e = cudaErrorInvalidConfiguration;
+  return e;
+}
+
+cudaError_t launch_emu_slice_operator(long long N, int n, const double *A_diag, const double *A_sub,
+                                      const EmuBuffers &b, DevStatus *st, cudaStream_t s) {
+  const int groups = (n + kRowsPerCta - 1) / kRowsPerCta;
+  const long long grid = N * groups;
+  const size_t sm = (size_t)3 * kRowsPerCta * n * sizeof(double);
+  k_emu_slice_operator<<<(unsigned)grid, 256, sm, s>>>(N, n, emu_np(n), A_diag, A_sub, b.Aslc, b.Aexp, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emu_residual(long long N, int n, int d, const double *X, const double *B, float *R32,
+                                double *R64, const EmuBuffers &b, DevStatus *st, long long timeout_ns, int sms,
+                                cudaStream_t s) {
+  if (d < 1 || d > kEmuDp) return cudaErrorInvalidValue;
+  const int np = emu_np(n);
+  cudaError_t e = cudaMemsetAsync(b.xmax, 0, kEmuDp * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const long long rows = N * n;
+  long long gx = (rows + 15) / 16;
+  if (gx > 4 * (long long)sms) gx = 4 * (long long)sms;
+  k_emu_xmax<<<(unsigned)gx, 256, 0, s>>>(rows, d, X, b.xmax);
+  k_emu_slice_x<<<(unsigned)N, 256, (size_t)n * d * sizeof(double), s>>>(N, n, np, d, X, b.xmax, b.xexp, b.Xslc);
+  EmuKArgs k;
+  k.N = N;
+  k.n = n;
+  k.np = np;
+  k.d = d;
+  k.Aexp = b.Aexp;
+  k.xexp = b.xexp;
+  k.X = X;
+  k.B = B;
+  k.R32 = R32;
+  k.R64 = R64;
+  k.st = st;
+  k.timeout_ns = timeout_ns;
+  const long long tiles = N * ((n + kM - 1) / kM);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  k_emu_residual<<<grid, kEmuThreads, kResidualSmem, s>>>(b.maps[0], b.maps[1], k);
+  return cudaGetLastError();
+}
+
+}  // namespace bdss

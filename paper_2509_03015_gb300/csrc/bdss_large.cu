@@ -20,13 +20,17 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
   if (sub == kSubA1) {
     for (long long m = rank; m < nE; m += gridDim.x)
       if (!largeA1(a, l, 2 * m + 1, smem, s_flag)) return false;
+  } else if (sub == kSubA2 && !factor && a.Li) {
+    // solve pass with the stored inverses: row tiles of y_j = L_j^{-1} b_j
+    const int nt = ntiles(n);
+    for (long long t = rank; t < nE * nt; t += gridDim.x) largeA2_inv(a, l, 2 * (t / nt) + 1, (int)(t % nt), smem);
   } else if (sub == kSubA2) {
     const int VT = vec_tile(sizeof(T));
-    const int nvt = ((factor ? 2 * n : 0) + d + VT - 1) / VT;
+    const int nvt = (largeA2_slots(a, factor) + VT - 1) / VT;
     for (long long t = rank; t < nE * nvt; t += gridDim.x) {
       const long long j = 2 * (t / nvt) + 1;
       const int v = (int)(t % nvt);
-      if (v * VT < largeA2_vectors(a, l, j, factor)) largeA2(a, l, j, v, factor, smem);
+      if (largeA2_live(a, l, j, factor, v * VT)) largeA2(a, l, j, v, factor, smem);
     }
   } else if (sub == kSubB) {
     if constexpr (kTc) {
@@ -290,12 +294,13 @@ cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStre
   return cudaGetLastError();
 }
 
-long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32) {
+long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32, int inv) {
   const long long Nl = p.Nl[l], nE = Nl / 2, nS = (Nl + 1) / 2;
   if (sub == kSubA1 || sub == kSubC) return nE;
   if (sub == kSubA2) {
+    if (!factor && inv) return nE * ntiles(p.n);
     const int VT = vec_tile(esz);
-    return nE * (((factor ? 2 * p.n : 0) + d + VT - 1) / VT);
+    return nE * (((factor ? (inv ? 3 : 2) * p.n : 0) + d + VT - 1) / VT);
   }
   if (tf32 && factor) return nS * (largeB_tc_tiles(p.n) + largeB_tiles(p.n, false, d));
   return nS * largeB_tiles(p.n, factor != 0, d);

@@ -144,6 +144,34 @@ __device__ void gemm_nt_narrow(T (&acc)[4], const VA &A, int r0, const VB &B, in
   }
 }
 
+// The narrow product with the left operand given transposed, row-major in
+// global memory: acc[j] += sum_k At[k * ld + r0 + tr] B(c0 + 4 tc + j, k) for
+// rows r0 + tr < M (zero beyond M or K).  The staging reads rows of At, so
+// its loads are coalesced (the products L^{-T} t of the downward pass).
+template <typename T, typename VB>
+__device__ void gemm_tn_narrow(T (&acc)[4], const T *At, long long ld, int M, int r0, const VB &B, int c0, int K,
+                               T *sA, T *sB) {
+  const int tr = threadIdx.x >> 2, tc = threadIdx.x & 3;
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+    for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
+      const int k = e / kTile, m = e - k * kTile;
+      sA[k * kTilePad + m] = (k0 + k < K && r0 + m < M) ? ldcg(At + (long long)(k0 + k) * ld + r0 + m) : T(0);
+    }
+    for (int e = threadIdx.x; e < kNarrow * kKc; e += blockDim.x) {
+      const int m = e / kKc, k = e - m * kKc;
+      sB[k * (kNarrow + 1) + m] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
+    }
+    __syncthreads();
+    const int kc = min(kKc, K - k0);
+    for (int k = 0; k < kc; ++k) {
+      const T a = sA[k * kTilePad + tr];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fma(a, sB[k * (kNarrow + 1) + 4 * tc + j], acc[j]);
+    }
+    __syncthreads();
+  }
+}
+
 // Shared memory (in elements of FP64) of the FP64 top block: d solution
 // vectors plus the tile work area (it never stages coupling vectors).
 __host__ __device__ inline size_t smem_large_top(int n, int d) {
@@ -338,15 +366,28 @@ __device__ bool largeA1(const Args<T> &a, int l, long long j, T *smem, int *s_fl
 }
 
 // Number of vectors of eliminated position j's forward substitution.
+// Vector slots of an eliminated block's forward substitution: the couplings
+// (2 n, the 64-vector tiles are laid out as if the right coupling existed),
+// the n unit vectors whose solutions are the columns of L^{-1} (factor with
+// an inverse buffer), then the RHS columns.
 template <typename T>
-__device__ __forceinline__ int largeA2_vectors(const Args<T> &a, int l, long long j, bool factor) {
-  const int n = a.p.n;
-  const bool hasR = (j + 1 < a.p.Nl[l]);
-  return (factor ? (hasR ? 2 * n : n) : 0) + a.d;
+__device__ __forceinline__ int largeA2_slots(const Args<T> &a, bool factor) {
+  return (factor ? (a.Li ? 3 : 2) * a.p.n : 0) + a.d;
 }
 
-// A2: vector tile v of eliminated position j: vectors are E_L's columns,
-// E_R's rows (if any), then the RHS columns.
+// Number of vectors of eliminated position j's forward substitution.
+template <typename T>
+__device__ __forceinline__ bool largeA2_live(const Args<T> &a, int l, long long j, bool factor, int c0) {
+  const int n = a.p.n;
+  const bool hasR = (j + 1 < a.p.Nl[l]);
+  // a vector tile is idle only when it holds nothing but the absent E_R rows
+  return !(factor && !hasR && c0 >= n && c0 + vec_tile(sizeof(T)) <= 2 * n);
+}
+
+// A2: vector tile v of eliminated position j.  Slots [0, n) are E_L's
+// columns, [n, 2n) E_R's rows (absent for the last block of a level: those
+// slots are skipped), [2n, 3n) the unit vectors of L^{-1} (with an inverse
+// buffer), then the RHS columns; in a solve pass only the RHS columns.
 template <typename T>
 __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor, T *smem) {
   const int n = a.p.n, d = a.d, lv = n + 1;
@@ -354,9 +395,11 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
   const bool hasR = (j + 1 < Nl);
   const long long orig = j << l;
   const size_t nn = (size_t)n * n;
-  const int nW = factor ? (hasR ? 2 * n : n) : 0;
+  const int nW = factor ? 2 * n : 0;              // coupling slots
+  const int nI = (factor && a.Li) ? n : 0;        // unit-vector slots
   const int VT = vec_tile(sizeof(T));
-  const int c0 = v * VT, nv = min(VT, nW + d - c0);
+  const int slots = nW + nI + d;
+  const int c0 = v * VT, nv = min(VT, slots - c0);
   T *sV = smem;
   T *work = sV + (size_t)VT * lv;
   const T *E = (l == 0) ? nullptr : a.Eb + (size_t)a.p.off[l] * nn;  // couplings formed at level l-1
@@ -367,11 +410,15 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
     if (c < nW && c < n) {  // column c of A_{j,j-1}
       val = (l == 0) ? (T)ldcg(a.A_sub + (size_t)(j - 1) * nn + (size_t)i * n + c)
                      : ldcg(E + (size_t)(j - 1) * nn + (size_t)i * n + c);
-    } else if (c < nW) {  // row c - n of A_{j+1,j}
+    } else if (c < nW) {  // row c - n of A_{j+1,j} (zero for the last block)
       const int r = c - n;
-      val = (l == 0) ? (T)ldcg(a.A_sub + (size_t)j * nn + (size_t)r * n + i) : ldcg(E + (size_t)j * nn + (size_t)r * n + i);
+      val = !hasR ? T(0)
+                  : (l == 0) ? (T)ldcg(a.A_sub + (size_t)j * nn + (size_t)r * n + i)
+                             : ldcg(E + (size_t)j * nn + (size_t)r * n + i);
+    } else if (c < nW + nI) {  // unit vector e_{c - nW}
+      val = (i == c - nW) ? T(1) : T(0);
     } else {  // RHS column
-      const int k = c - nW;
+      const int k = c - nW - nI;
       const size_t bo = (size_t)orig * n * d + (size_t)i * d + k;
       if (l == 0 && a.B64) val = (T)ldcg(a.B64 + bo);
       else if (l == 0 && a.Bt) val = ldcg(a.Bt + bo);
@@ -387,10 +434,54 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
     const int cc = e / n, i = e - cc * n, c = c0 + cc;
     const T val = sV[(size_t)cc * lv + i];
     if (c < nW && c < n) W[(size_t)(j - 1) * nn + (size_t)c * n + i] = val;
-    else if (c < nW) W[(size_t)j * nn + (size_t)(c - n) * n + i] = val;
-    else a.Y[(size_t)orig * n * d + (size_t)i * d + (c - nW)] = val;
+    else if (c < nW) { if (hasR) W[(size_t)j * nn + (size_t)(c - n) * n + i] = val; }
+    else if (c >= nW + nI) a.Y[(size_t)orig * n * d + (size_t)i * d + (c - nW - nI)] = val;
+  }
+  if (nI) {
+    // columns u0..u1-1 of L^{-1}, row-major in Li: consecutive threads take
+    // consecutive columns of one row
+    const int u0 = max(c0, nW) - nW, u1 = min(c0 + nv, nW + nI) - nW;
+    if (u1 > u0) {
+      T *Li = a.Li + (size_t)orig * nn;
+      const int nu = u1 - u0;
+      for (int e = threadIdx.x; e < n * nu; e += blockDim.x) {
+        const int i = e / nu, u = u0 + e - i * nu;
+        Li[(size_t)i * n + u] = sV[(size_t)(u + nW - c0) * lv + i];
+      }
+    }
   }
   __syncthreads();
+}
+
+// Solve pass with the stored inverses: row tile R of y_j = L_j^{-1} b_j (rows
+// 64 R .. 64 R + 63, all RHS columns) into Yt; L^{-1} is lower triangular,
+// so the product stops at column 64 R + 63.
+template <typename T>
+__device__ void largeA2_inv(const Args<T> &a, int l, long long j, int R, T *smem) {
+  const int n = a.p.n, d = a.d;
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  T *sA = smem, *sB = sA + kKc * kTilePad;
+  const int r0 = R * kTile, K = min(n, r0 + kTile);
+  const View<T> Lr{a.Li + (size_t)orig * nn, n, 1, n, n};  // (r, k) -> L^{-1}[r][k]
+  for (int c0 = 0; c0 < d; c0 += kNarrow) {
+    T acc[4] = {};
+    // b_j as the right operand: (c, k) -> b[k][c]
+    if (l == 0 && a.B64) {
+      const View<double> Bv{a.B64 + (size_t)orig * nd + c0, 1, d, d - c0, n};
+      gemm_nt_narrow(acc, Lr, r0, Bv, 0, K, sA, sB);
+    } else {
+      const T *src = (l == 0 && a.Bt) ? a.Bt : a.Y;
+      const View<T> Bv{src + (size_t)orig * nd + c0, 1, d, d - c0, n};
+      gemm_nt_narrow(acc, Lr, r0, Bv, 0, K, sA, sB);
+    }
+    const int r = r0 + (threadIdx.x >> 2);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int c = c0 + 4 * (threadIdx.x & 3) + jj;
+      if (r < n && c < d) a.Yt[(size_t)orig * nd + (size_t)r * d + c] = acc[jj];
+    }
+  }
 }
 
 // Tiles of a separator's phase-B work.
@@ -454,8 +545,9 @@ __device__ void largeB(const Args<T> &a, int l, long long k, int t, bool factor,
     for (int c0 = 0; c0 < d; c0 += kNarrow) {
       T acc[4] = {};
       // y as the "B" operand: (c, q) -> y[q][c]
-      const View<T> Ym{a.Y + (size_t)((s - 1) << l) * n * d + c0, 1, d, d - c0, n};
-      const View<T> Yp{a.Y + (size_t)((s + 1) << l) * n * d + c0, 1, d, d - c0, n};
+      const T *ys = a.Yt ? a.Yt : a.Y;  // where this pass keeps y of the eliminated blocks
+      const View<T> Ym{ys + (size_t)((s - 1) << l) * n * d + c0, 1, d, d - c0, n};
+      const View<T> Yp{ys + (size_t)((s + 1) << l) * n * d + c0, 1, d, d - c0, n};
       if (hasM) gemm_nt_narrow(acc, W0, ti * kTile, Ym, 0, n, sA, sB);
       if (hasP) gemm_nt_narrow(acc, W1, ti * kTile, Yp, 0, n, sA, sB);
       const int r = ti * kTile + (threadIdx.x >> 2);
@@ -563,7 +655,7 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
   T *work = sV + (size_t)d * lv;
   T *sA = work + kTile * kTilePad, *sB = sA + kKc * kTilePad;
   const T *W = a.Wb + (size_t)a.p.off[l] * nn;
-  const T *Yj = a.Y + (size_t)orig * nd;
+  const T *Yj = (a.Yt ? a.Yt : a.Y) + (size_t)orig * nd;
   // t[q][c] = y[q][c] - sum_p W_L[q][p] x_{j-1}[p][c] - sum_p W_R[q][p] x_{j+1}[p][c],
   // W_L[q][p] = Wt_L[p][q]
   const View<T> WLq{W + (size_t)(j - 1) * nn, 1, n, n, n};
@@ -585,8 +677,37 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
       }
       __syncthreads();
     }
-  trsv_bwd_blocked(a.Ld + (size_t)orig * nn, n, sV, d, work);
   T *Yo = a.Y + (size_t)orig * nd;
+  if (a.Li) {
+    // x = L^{-T} t as row tiles of products with the stored inverse:
+    // x[r] = sum_{k >= r} L^{-1}[k][r] t[k]; t stays in shared memory, x goes
+    // straight to Y (and X64)
+    const T *Li = a.Li + (size_t)orig * nn;
+    for (int R = 0; R < ntiles(n); ++R) {
+      const int r0 = R * kTile;
+      for (int c0 = 0; c0 < d; c0 += kNarrow) {
+        T acc[4] = {};
+        const View<T, true> Tv{sV + (size_t)c0 * lv + r0, lv, 1, d - c0, n - r0};  // (c, k) -> t[r0 + k][c0 + c]
+        gemm_tn_narrow(acc, Li + (size_t)r0 * n, n, n, r0, Tv, 0, n - r0, sA, sB);
+        const int r = r0 + (threadIdx.x >> 2);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int c = c0 + 4 * (threadIdx.x & 3) + jj;
+          if (r < n && c < d) {
+            const size_t o = (size_t)r * d + c;
+            Yo[o] = acc[jj];
+            if (a.X64) {
+              double *xo = a.X64 + (size_t)orig * nd + o;
+              *xo = a.x_accumulate ? *xo + (double)acc[jj] : (double)acc[jj];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  trsv_bwd_blocked(a.Ld + (size_t)orig * nn, n, sV, d, work);
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
     const int i = e / d, c = e - i * d;
     const T x = sV[(size_t)c * lv + i];

@@ -40,7 +40,9 @@ cudaError_t launch_large_persistent(const Args<T> &a, int factor, int rhs, int g
 template <typename T>
 cudaError_t launch_large_sub(const Args<T> &a, int l, int sub, int factor, int grid, size_t smem, cudaStream_t s);
 template <typename T> cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStream_t s);
-long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32);
+// Tasks of sub-phase `sub` at level l; inv = the pass uses the stored
+// inverses (FP32 tiled path).
+long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32, int inv);
 cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows, int n);
 cudaError_t run_tc_selftest(double *max_err, int *status);
 cudaError_t launch_residual_rows(long long N, int n, int d, const double *A_diag, const double *A_sub,

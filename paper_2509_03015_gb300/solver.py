@@ -126,6 +126,17 @@ class Solver:
                    "bdss_last_refine_stats")
         return p.value, c.value
 
+    def residual(self, B, X, R=None):
+        """R = B - A X for the last factored A (the refinement's residual:
+        on the tensor cores where the handle supports it, else FP64 ALU)."""
+        _check_tensor(B, "B", host_ok=True)
+        _check_tensor(X, "X", tuple(B.shape), host_ok=True)
+        if R is None:
+            R = torch.empty(B.shape, dtype=torch.float64, device="cuda")
+        _check_tensor(R, "R", tuple(B.shape))
+        _lib.check(self.lib.bdss_residual(self.h, _ptr(B), _ptr(X), B.shape[-1], _ptr(R)), "bdss_residual")
+        return R
+
     def kernel_times(self):
         """{class: (ms, launches)} of the last call, timed with CUDA events on
         the handle's stream (set_option("kernel_timing", 1) first)."""

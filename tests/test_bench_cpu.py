@@ -26,10 +26,14 @@ def test_profiled_traffic_follows_the_committed_capture():
 
 def test_kernel_rooflines_from_class_times():
     # residual: 6 n^2 d N flops per launch; two launches of 1 ms each
-    kt = {"residual": (2.0, 2), "correction": (4.0, 2), "solve": (0.0, 0)}
-    r = bench.kernel_rooflines(kt, N=100, n=8, d=2, mode="fp32_ir", sms=152, mhz=2070)
-    assert set(r) == {"residual", "correction"}
+    # over 2 steps: 4 residual launches (2 per step) of 1 ms, 2 corrections
+    kt = {"residual": (4.0, 4), "correction": (4.0, 2), "solve": (0.0, 0), "factor": (30.0, 74)}
+    units = {"residual": 2, "correction": 1, "factor": 1}
+    r = bench.kernel_rooflines(kt, 2, units, N=100, n=8, d=2, mode="fp32_ir", sms=152, mhz=2070)
+    assert set(r) == {"residual", "correction", "factor"}
     assert r["residual"]["achieved"] == pytest.approx(6 * 64 * 2 * 100 / 1e-3 / 1e12)
+    # a factorisation split over many launches still counts once per step
+    assert r["factor"]["ms_per_unit"] == pytest.approx(15.0)
     assert r["residual"]["frac"] == pytest.approx(r["residual"]["achieved"] / r["residual"]["peak"])
     assert r["correction"]["bound"] == "hbm" and r["correction"]["unit"] == "GB/s"
 
