@@ -233,6 +233,49 @@ bdss_status bdss_kalman_assemble(int64_t N, int32_t n, int32_t m, int32_t rinv_d
                                  const double *Rinv, const double *z, const double *zeta,
                                  double *A_diag, double *A_sub, double *B, void *cuda_stream);
 
+/*
+ * Partitioned solve of one system over several ranks (the separator /
+ * interior partition of Sec. 3.1, Eq. 2-4, applied once at the top level):
+ * the N blocks are cut into contiguous chunks, the last block of every chunk
+ * but the last is a separator, and each rank eliminates the interior of its
+ * chunk (the blocks between its left and right separators) with this handle.
+ * The separators then form a block-tridiagonal reduced system (Eq. 5):
+ *   S_ss    = A_ss - (S_RR of the interior on its left) - (S_LL of the one on its right)
+ *   S_{s',s} = -(S_RL of the interior between s and the next separator s')
+ *   b_hat_s = b_s - (b_R of the interior on its left) - (b_L of the one on its right)
+ * which every rank solves after one exchange of the contributions, and
+ * bdss_chunk_backsolve recovers the interior.
+ *
+ * bdss_chunk_reduce: factors the interior (A_diag: N x n x n, A_sub:
+ * (N-1) x n x n, as bdss_factor; N and n are the handle's, FP64 handles only,
+ * else BDSS_ERR_UNSUPPORTED) and returns its contribution to the reduced
+ * system.  A_left = A_{first, sL}, the n x n coupling of the first interior
+ * block to the left separator (the global sub-diagonal block above the
+ * interior), or NULL if there is no left separator; A_right = A_{sR, last},
+ * the coupling of the right separator to the last interior block (the global
+ * sub-diagonal block below it), or NULL.  B: the interior's right-hand side,
+ * N x n x d, 1 <= d <= d_max.  Outputs (device, row-major):
+ *   S     = [S_LL, S_RR, S_RL], 3 x n x n:
+ *           S_LL = A_left^T (A_I^{-1})_{first,first} A_left,
+ *           S_RR = A_right (A_I^{-1})_{last,last} A_right^T,
+ *           S_RL = A_right (A_I^{-1})_{last,first} A_left   (zero when absent);
+ *   b_hat = [b_L, b_R], 2 x n x d: A_left^T (A_I^{-1} B)_first, A_right (A_I^{-1} B)_last.
+ * The factors stay in the handle for bdss_chunk_backsolve.  Allocates
+ * stream-ordered temporaries of 2 N n min(n, d_max) doubles (BDSS_ERR_ALLOC)
+ * and synchronises the stream.
+ *
+ * bdss_chunk_backsolve: X = A_I^{-1} (B - E_first A_left x_left -
+ * E_last A_right^T x_right) with the stored factors; x_left, x_right: the
+ * separators' solution blocks (n x d, device), required where the matching
+ * coupling is given.  X: N x n x d device memory.  Allocates N n d doubles
+ * stream-ordered and synchronises.
+ */
+bdss_status bdss_chunk_reduce(bdss_handle h, const double *A_diag, const double *A_sub, const double *A_left,
+                              const double *A_right, const double *B, int32_t d, double *S, double *b_hat,
+                              bdss_info *info);
+bdss_status bdss_chunk_backsolve(bdss_handle h, const double *B, const double *A_left, const double *A_right,
+                                 const double *x_left, const double *x_right, int32_t d, double *X);
+
 /* Number of grid barriers / kernel launches the last factor or solve issued
  * (host pointers, either may be NULL). */
 bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int64_t *grid_barriers);

@@ -48,6 +48,8 @@ SIGNATURES = {
     "bdss_last_cuda_error": (ctypes.c_char_p, []),
     "bdss_last_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
     "bdss_residual": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "bdss_chunk_reduce": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _info_p]),
+    "bdss_chunk_backsolve": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
     "bdss_tc_selftest": (_i32, [ctypes.POINTER(ctypes.c_double)]),
     "bdss_adjoint_grads": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
     "bdss_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i32), _i32, _vp]),

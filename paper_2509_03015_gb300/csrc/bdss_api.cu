@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/bdss.h"
+#include "bdss_chunk.h"
 #include "bdss_emu.h"
 #include "bdss_launch.h"
 #include "bdss_kalman.h"
@@ -1041,6 +1042,109 @@ bdss_status bdss_last_trace(bdss_handle h, int64_t *release_ns, int32_t capacity
   const int c = std::min(h->trace_count, (int)capacity);
   for (int i = 0; i < c; ++i) release_ns[i] = h->trace[i];
   if (count) *count = h->trace_count;
+  return BDSS_OK;
+}
+
+// Stream-ordered temporary of the partitioned-solve entry points (counted
+// by the allocation-failure hook).
+static bool tmp_alloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (inject_alloc_failure() || cudaMallocAsync(p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+static bool opt_block_ok(const double *p) { return !p || (aligned16(p) && device_readable(p)); }
+
+bdss_status bdss_chunk_reduce(bdss_handle h, const double *A_diag, const double *A_sub, const double *A_left,
+                              const double *A_right, const double *B, int32_t d, double *S, double *b_hat,
+                              bdss_info *info) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  info_init(info);
+  if (is_mixed(h)) return BDSS_ERR_UNSUPPORTED;
+  bdss_status st = check_factor_args(h, A_diag, A_sub);
+  if (st != BDSS_OK) return st;
+  if (!B || !aligned16(B) || !device_readable(B) || d < 1 || d > h->d_max) return BDSS_ERR_INVALID_ARG;
+  if (!S || !b_hat || !aligned16(S) || !aligned16(b_hat) || !device_memory(S) || !device_memory(b_hat))
+    return BDSS_ERR_INVALID_ARG;
+  if (!opt_block_ok(A_left) || !opt_block_ok(A_right)) return BDSS_ERR_INVALID_ARG;
+  st = factor_impl(h, A_diag, A_sub, nullptr, nullptr, 0, info);
+  if (st != BDSS_OK) return st;
+  const long long N = h->N;
+  const int n = h->n, dc = std::min(n, h->d_max);
+  const size_t nn = (size_t)n * n;
+  cudaStream_t s = h->stream;
+  double *Z = nullptr, *Zs = nullptr;
+  const size_t words = (size_t)N * n * std::max(dc, (int)d);
+  t_alloc_count = 0;
+  if (!tmp_alloc((void **)&Z, words * sizeof(double), s) || !tmp_alloc((void **)&Zs, words * sizeof(double), s)) {
+    if (Z) cudaFreeAsync(Z, s);
+    return BDSS_ERR_ALLOC;
+  }
+  cudaError_t e = cudaMemsetAsync(S, 0, 3 * nn * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b_hat, 0, (size_t)2 * n * d * sizeof(double), s);
+  const double *last = nullptr;
+  // y = A_I^{-1} B, then b_hat = [A_left^T y_first, A_right y_last]
+  if (e == cudaSuccess) {
+    st = bdss_solve(h, B, Zs, d, nullptr);
+    if (st != BDSS_OK) e = cudaErrorUnknown;
+  }
+  last = Zs + (size_t)(N - 1) * n * d;
+  if (e == cudaSuccess && A_left) e = launch_chunk_product(n, d, A_left, 1, Zs, b_hat, d, 0, s);
+  if (e == cudaSuccess && A_right) e = launch_chunk_product(n, d, A_right, 0, last, b_hat + (size_t)n * d, d, 0, s);
+  // the couplings, dc columns at a time:
+  //   S_LL = A_left^T (A_I^{-1})_{first,first} A_left, S_RL = A_right (A_I^{-1})_{last,first} A_left,
+  //   S_RR = A_right (A_I^{-1})_{last,last} A_right^T
+  for (int c0 = 0; c0 < n && e == cudaSuccess && st == BDSS_OK; c0 += dc) {
+    const int m = std::min(dc, n - c0);
+    const double *zl = Zs + (size_t)(N - 1) * n * m;
+    if (A_left) {
+      e = launch_chunk_rhs(N, n, m, 0, A_left, 0, c0, Z, s);
+      if (e == cudaSuccess) st = bdss_solve(h, Z, Zs, m, nullptr);
+      if (e == cudaSuccess && st == BDSS_OK) e = launch_chunk_product(n, m, A_left, 1, Zs, S, n, c0, s);
+      if (e == cudaSuccess && st == BDSS_OK && A_right)
+        e = launch_chunk_product(n, m, A_right, 0, zl, S + 2 * nn, n, c0, s);
+    }
+    if (A_right && e == cudaSuccess && st == BDSS_OK) {
+      e = launch_chunk_rhs(N, n, m, (int)(N - 1), A_right, 1, c0, Z, s);
+      if (e == cudaSuccess) st = bdss_solve(h, Z, Zs, m, nullptr);
+      if (e == cudaSuccess && st == BDSS_OK) e = launch_chunk_product(n, m, A_right, 0, zl, S + nn, n, c0, s);
+    }
+  }
+  cudaFreeAsync(Z, s);
+  cudaFreeAsync(Zs, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  if (st != BDSS_OK) return st;
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e);
+  return BDSS_OK;
+}
+
+bdss_status bdss_chunk_backsolve(bdss_handle h, const double *B, const double *A_left, const double *A_right,
+                                 const double *x_left, const double *x_right, int32_t d, double *X) {
+  if (!h) return BDSS_ERR_INVALID_ARG;
+  if (is_mixed(h)) return BDSS_ERR_UNSUPPORTED;
+  bdss_status st = check_solve_args(h, B, X, d);
+  if (st != BDSS_OK) return st;
+  if (!opt_block_ok(A_left) || !opt_block_ok(A_right)) return BDSS_ERR_INVALID_ARG;
+  if ((A_left && !opt_block_ok(x_left)) || (A_right && !opt_block_ok(x_right)) || (A_left && !x_left) ||
+      (A_right && !x_right))
+    return BDSS_ERR_INVALID_ARG;
+  if (!h->factored) return BDSS_ERR_NOT_FACTORED;
+  cudaStream_t s = h->stream;
+  double *Bp = nullptr;
+  t_alloc_count = 0;
+  if (!tmp_alloc((void **)&Bp, (size_t)h->N * h->n * d * sizeof(double), s)) return BDSS_ERR_ALLOC;
+  cudaError_t e = launch_chunk_fix_rhs(h->N, h->n, d, B, A_left, A_right, x_left, x_right, Bp, s);
+  if (e == cudaSuccess) st = bdss_solve(h, Bp, X, d, nullptr);
+  cudaFreeAsync(Bp, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (st != BDSS_OK) return st;
+  if (e2 != cudaSuccess) return cuda_fail(e2);
   return BDSS_OK;
 }
 

@@ -137,6 +137,41 @@ class Solver:
         _lib.check(self.lib.bdss_residual(self.h, _ptr(B), _ptr(X), B.shape[-1], _ptr(R)), "bdss_residual")
         return R
 
+    def chunk_reduce(self, A_diag, A_sub, A_left, A_right, B):
+        """Eliminate this handle's chunk interior (partitioned solve): returns
+        S = [S_LL, S_RR, S_RL] (3, n, n) and b_hat = [b_L, b_R] (2, n, d), the
+        interior's contribution to the reduced system of its separators.
+        A_left / A_right: the n x n couplings to the left / right separator,
+        or None."""
+        sd, ss, _ = self._shapes(1)
+        _check_tensor(A_diag, "A_diag", sd, host_ok=True)
+        if self.N > 1:
+            _check_tensor(A_sub, "A_sub", ss, host_ok=True)
+        for t, nm in ((A_left, "A_left"), (A_right, "A_right")):
+            if t is not None:
+                _check_tensor(t, nm, (self.n, self.n), host_ok=True)
+        d = B.shape[-1]
+        _check_tensor(B, "B", self._shapes(d)[2], host_ok=True)
+        S = torch.empty((3, self.n, self.n), dtype=torch.float64, device="cuda")
+        bh = torch.empty((2, self.n, d), dtype=torch.float64, device="cuda")
+        info = _lib.bdss_info()
+        st = self.lib.bdss_chunk_reduce(self.h, _ptr(A_diag), _ptr(A_sub if self.N > 1 else None), _ptr(A_left),
+                                        _ptr(A_right), _ptr(B), d, _ptr(S), _ptr(bh), ctypes.byref(info))
+        _lib.check(st, "bdss_chunk_reduce", info)
+        self._keep = (A_diag, A_sub)
+        return S, bh
+
+    def chunk_backsolve(self, B, A_left, A_right, x_left, x_right):
+        """The chunk interior's solution once its separators' blocks are
+        known (after chunk_reduce on this handle)."""
+        d = B.shape[-1]
+        _check_tensor(B, "B", self._shapes(d)[2], host_ok=True)
+        X = torch.empty(B.shape, dtype=torch.float64, device="cuda")
+        st = self.lib.bdss_chunk_backsolve(self.h, _ptr(B), _ptr(A_left), _ptr(A_right), _ptr(x_left),
+                                           _ptr(x_right), d, _ptr(X))
+        _lib.check(st, "bdss_chunk_backsolve")
+        return X
+
     def kernel_times(self):
         """{class: (ms, launches)} of the last call, timed with CUDA events on
         the handle's stream (set_option("kernel_timing", 1) first)."""
