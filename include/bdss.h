@@ -117,6 +117,14 @@ typedef enum {
                                    first use; at most 4 cycles, each restarted from the
                                    true FP64 residual */
   BDSS_OPT_MAX_KRYLOV_ITERS = 8, /* mixed precision: CG iterations per cycle (default 300) */
+  BDSS_OPT_SHIFT = 11,          /* mixed precision: 1 (default) = when an FP32 pivot fails
+                                   (kappa(A) beyond about 1/u_32), factor A + sigma diag(A)
+                                   instead, sigma = 2^-20 growing 16x per failure up to
+                                   2^-4 (bdss_factor_shift reports it), and refine with
+                                   FP64 CG on the unshifted A from the first correction
+                                   (unless BDSS_OPT_REFINE_KRYLOV = 0); the copy of A_diag
+                                   (N n^2 doubles) is allocated on first use.
+                                   0 = return BDSS_ERR_NOT_SPD */
   BDSS_OPT_RESIDUAL_EMU = 10,   /* mixed precision, 64 < n <= 256 and d_max <= 16: 1 (default)
                                    = the FP64 residual of the refinement on the tensor cores
                                    (BF16 digit slices, exact FP32 accumulation: see
@@ -286,6 +294,11 @@ bdss_status bdss_last_launch_stats(bdss_handle h, int64_t *kernel_launches, int6
  * it off.  The call must then return BDSS_ERR_ALLOC; bdss_create frees what
  * it had allocated, a solve keeps its buffers for bdss_destroy. */
 bdss_status bdss_debug_fail_alloc(int32_t k);
+
+/* Relative diagonal shift sigma of the handle's stored factors (mixed
+ * precision: the factors are those of A + sigma diag(A); 0 when the
+ * unshifted FP32 factorisation succeeded).  Host pointer. */
+bdss_status bdss_factor_shift(bdss_handle h, double *sigma);
 
 /* Refinement steps of the handle's last mixed-precision solve (host pointers,
  * either may be NULL): plain corrections X += M^-1 r and preconditioned-CG

@@ -18,7 +18,7 @@ STATUS_NAMES = {
 PRECISIONS = {"fp64": 0, "fp32_ir": 1, "tf32_ir": 2}
 OPTIONS = {"timeout_ms": 0, "persistent": 1, "max_refine": 2, "target_berr_e18": 3, "debug_skip_arrive": 4,
            "debug_guards": 5, "debug_corrupt_guard": 6, "refine_krylov": 7, "max_krylov_iters": 8,
-           "kernel_timing": 9, "residual_emu": 10}
+           "kernel_timing": 9, "residual_emu": 10, "shift": 11}
 KERNEL_CLASSES = ("factor", "schur_tc", "solve", "correction", "residual", "krylov", "slice")
 
 
@@ -48,6 +48,7 @@ SIGNATURES = {
     "bdss_last_cuda_error": (ctypes.c_char_p, []),
     "bdss_last_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
     "bdss_residual": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "bdss_factor_shift": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "bdss_chunk_reduce": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _info_p]),
     "bdss_chunk_backsolve": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
     "bdss_tc_selftest": (_i32, [ctypes.POINTER(ctypes.c_double)]),

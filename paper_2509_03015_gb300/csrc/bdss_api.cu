@@ -65,6 +65,10 @@ struct bdss_ctx {
   double *kr_R = nullptr, *kr_Z = nullptr, *kr_P = nullptr, *kr_Q = nullptr;
   double *kr_part = nullptr, *kr_sc = nullptr;
   int last_plain = 0, last_cg = 0;  // refinement steps of the last solve
+  // mixed precision: shifted factorisation when an FP32 pivot fails
+  int shift_on = 1;
+  double shift_used = 0.0;   // relative diagonal shift of the stored factors
+  double *Ashift = nullptr;  // shifted copy of A_diag (allocated on first use)
   // mixed precision, tiled path: the FP64-accurate residual on the tensor
   // cores (sliced operator built once per factorisation)
   EmuBuffers emu{};
@@ -393,6 +397,7 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->Y32);
   cudaFree(h->R32);
   cudaFree(h->partial);
+  cudaFree(h->Ashift);
   cudaFree(h->kr_R);
   cudaFree(h->kr_Z);
   cudaFree(h->kr_P);
@@ -537,6 +542,10 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
       if (value < 1 || value > 100000) return BDSS_ERR_INVALID_ARG;
       h->max_krylov = (int)value;
       return BDSS_OK;
+    case BDSS_OPT_SHIFT:
+      if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
+      h->shift_on = (int)value;
+      return BDSS_OK;
     case BDSS_OPT_RESIDUAL_EMU:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
       if (value && !h->emu_ready) return BDSS_ERR_UNSUPPORTED;
@@ -666,6 +675,45 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
   }
   if (e != cudaSuccess) return cuda_fail(e);
   bdss_status st = finish(h, info);
+  h->shift_used = 0.0;
+  if (st == BDSS_ERR_NOT_SPD && is_mixed(h) && h->shift_on) {
+    // kappa(A) u_32 near or above one: an FP32 pivot failed.  Factor
+    // A + sigma diag(A) instead (Higham and Pranesh's shifted low-precision
+    // Cholesky), sigma = 2^-20 (about 8 u_32) growing 16x per failure up to
+    // 2^-4; the FP64 CG refinement on the unshifted A, preconditioned by these
+    // factors, absorbs the shift.
+    if (!h->Ashift) {
+      t_alloc_count = 0;
+      if (!ws_alloc(h, (void **)&h->Ashift, (size_t)h->N * h->n * h->n * sizeof(double))) {
+        cudaGetLastError();
+        h->Ashift = nullptr;
+        return BDSS_ERR_ALLOC;
+      }
+    }
+    for (double sigma = 0x1p-20; sigma <= 0x1p-4 && st == BDSS_ERR_NOT_SPD; sigma *= 16.0) {
+      e = reset_status(h);
+      if (e == cudaSuccess) e = launch_shift_diag(h->N, h->n, A_diag, sigma, h->Ashift, h->sms, h->stream);
+      h->launches += 1;
+      Args<float> a = base_args<float>(h);
+      a.A_diag = h->Ashift;
+      a.A_sub = A_sub;
+      if (rhs) {
+        a.d = d;
+        a.B64 = B;
+        a.Y = h->Y32;
+        a.X64 = X;
+        a.x_accumulate = 0;
+      }
+      if (e == cudaSuccess) e = run_levels<float>(h, a, true, rhs);
+      if (e != cudaSuccess) return cuda_fail(e);
+      st = finish(h, info);
+      if (st == BDSS_OK) h->shift_used = sigma;
+    }
+    if (st == BDSS_OK && info) {
+      info->level = -1;
+      info->block = -1;
+    }
+  }
   if (st != BDSS_OK) return st;
   h->norm_valid = false;  // ||A||_inf comes with the first residual
   h->emu_sliced = false;  // the sliced operator is rebuilt from the new A
@@ -841,7 +889,8 @@ static bdss_status refine(bdss_ctx *h, const double *B, double *X, int d, bdss_i
     if (berr <= h->target) { result = BDSS_OK; break; }
     const bool stalled = it > 0 && !(berr < 0.5 * prev);
     const bool plain_done = stalled || it >= h->max_refine;
-    const bool cg = cycles > 0 || h->krylov == 2 || (h->krylov == 1 && plain_done);
+    // shifted factors are no accurate solver of A: CG from the first correction
+    const bool cg = cycles > 0 || h->krylov == 2 || (h->krylov == 1 && (plain_done || h->shift_used > 0));
     if (!cg) {
       if (plain_done) break;
       prev = berr;
@@ -1019,6 +1068,12 @@ bdss_status bdss_tc_selftest(double *max_rel_err) {
 bdss_status bdss_debug_fail_alloc(int32_t k) {
   if (k < 0) return BDSS_ERR_INVALID_ARG;
   g_fail_alloc.store(k);
+  return BDSS_OK;
+}
+
+bdss_status bdss_factor_shift(bdss_handle h, double *sigma) {
+  if (!h || !sigma) return BDSS_ERR_INVALID_ARG;
+  *sigma = h->shift_used;
   return BDSS_OK;
 }
 

@@ -226,4 +226,23 @@ cudaError_t launch_pcg_direction(long long rows, int d, const double *sc, const 
   return cudaGetLastError();
 }
 
+// Shifted copy of the diagonal blocks for the shifted FP32 factorisation:
+// out = A_diag with every diagonal entry scaled by (1 + sigma), i.e.
+// A + sigma diag(A) (the off-diagonal blocks are used unchanged).
+__global__ void k_shift_diag(long long N, int n, const double *A_diag, double sigma, double *out) {
+  const long long nn = (long long)n * n, total = N * nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long w = e % nn;
+    const double v = A_diag[e];
+    out[e] = (w / n == w % n) ? v + sigma * v : v;
+  }
+}
+
+cudaError_t launch_shift_diag(long long N, int n, const double *A_diag, double sigma, double *out, int sms,
+                              cudaStream_t s) {
+  k_shift_diag<<<4 * sms, 256, 0, s>>>(N, n, A_diag, sigma, out);
+  return cudaGetLastError();
+}
+
 }  // namespace bdss

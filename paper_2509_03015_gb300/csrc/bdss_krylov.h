@@ -25,6 +25,9 @@ int pcg_update_grid(long long rows);
 cudaError_t launch_pcg_update(long long rows, int d, const double *sc, const double *P, const double *Q, double *X,
                               double *R, double *part, int grid, cudaStream_t s);
 cudaError_t launch_pcg_scalars(int nparts, int d, const double *part, int step, double *sc, cudaStream_t s);
+// out = A_diag with the diagonal scaled by (1 + sigma): the shifted FP32 factorisation.
+cudaError_t launch_shift_diag(long long N, int n, const double *A_diag, double sigma, double *out, int sms,
+                              cudaStream_t s);
 cudaError_t launch_pcg_direction(long long rows, int d, const double *sc, const double *Z, double *P, int init,
                                  int sms, cudaStream_t s);
 

@@ -230,6 +230,28 @@ def laplace_btd(N: int, n: int, d: int, seed: int):
     return dict(A_diag=A_diag, A_sub=A_sub, B=np.ascontiguousarray(B))
 
 
+def illcond_btd(N: int, n: int, d: int, seed: int, kappa: float = 1e9):
+    """SPD system with condition number about kappa whose FP32 Cholesky
+    fails: every diagonal block is Q diag(lambda) Q^T with lambda spaced
+    log-uniformly from 1 down to 1/kappa (Q Haar), and A_{i+1,i} has 2-norm
+    1/(4 kappa), so the couplings move no eigenvalue by more than half of the
+    smallest.  Drawn from numpy.random.default_rng(seed) in the order Q (per
+    block), the couplings, B."""
+    rng = np.random.default_rng(seed)
+    lam = np.logspace(0.0, -math.log10(kappa), n)
+    A_diag = np.empty((N, n, n))
+    for i in range(N):
+        Q = haar_orthogonal(rng, n)
+        A_diag[i] = (Q * lam) @ Q.T
+        A_diag[i] = 0.5 * (A_diag[i] + A_diag[i].T)
+    A_sub = np.empty((max(N - 1, 0), n, n))
+    for i in range(N - 1):
+        G = rng.standard_normal((n, n))
+        A_sub[i] = G * (0.25 / kappa / np.linalg.norm(G, 2))
+    B = rng.standard_normal((N, n, d))
+    return dict(A_diag=A_diag, A_sub=A_sub, B=B)
+
+
 def tridiag_121(N: int, d: int = 1):
     """n = 1: A = tridiag(-1, 2, -1), B = all ones."""
     return dict(A_diag=np.full((N, 1, 1), 2.0), A_sub=np.full((max(N - 1, 0), 1, 1), -1.0),

@@ -172,6 +172,13 @@ class Solver:
         _lib.check(st, "bdss_chunk_backsolve")
         return X
 
+    def factor_shift(self):
+        """Relative diagonal shift sigma of the stored factors (mixed
+        precision; 0 unless the unshifted FP32 factorisation failed)."""
+        out = ctypes.c_double()
+        _lib.check(self.lib.bdss_factor_shift(self.h, ctypes.byref(out)), "bdss_factor_shift")
+        return out.value
+
     def kernel_times(self):
         """{class: (ms, launches)} of the last call, timed with CUDA events on
         the handle's stream (set_option("kernel_timing", 1) first)."""

@@ -28,3 +28,15 @@ def test_refine_options_and_stats_reject_bad_arguments():
     p, c = ctypes.c_int32(), ctypes.c_int32()
     assert lib.bdss_last_refine_stats(None, ctypes.byref(p), ctypes.byref(c)) == 1
     assert _lib.OPTIONS["refine_krylov"] == 7 and _lib.OPTIONS["max_krylov_iters"] == 8
+
+
+def test_illcond_generator_condition_number():
+    """The shifted-factorisation test input: kappa within a factor 4 of the
+    requested value (the couplings move eigenvalues by at most a quarter of
+    the smallest block eigenvalue each way)."""
+    from tests._helpers import dense_A
+    s = inputs.illcond_btd(6, 5, 1, seed=3, kappa=1e9)
+    ev = np.linalg.eigvalsh(dense_A(s["A_diag"], s["A_sub"]))
+    assert ev.min() > 0
+    k = ev.max() / ev.min()
+    assert 0.25e9 <= k <= 4e9

@@ -110,3 +110,31 @@ def test_zero_corrections_and_cg_allocation_failure():
         _check(s, X, 0.7 * N * N)
     finally:
         sol.close()
+
+
+@pytest.mark.parametrize("N,n,d,prec", [(64, 8, 2, "fp32_ir"), (33, 24, 1, "fp32_ir"), (9, 96, 2, "tf32_ir")])
+def test_shifted_factorisation_beyond_fp32(oracle_mod, N, n, d, prec):
+    """kappa ~ 1e9: the FP32 Cholesky fails (a pivot goes non-positive in
+    FP32), the default mode factors A + sigma diag(A) and the FP64 CG
+    refinement on the unshifted A reaches the backward-error bar; with the
+    shift switched off the call reports BDSS_ERR_NOT_SPD."""
+    from paper_2509_03015_gb300 import BDSSError, Solver
+    s = inputs.illcond_btd(N, n, d, seed=N + n, kappa=1e9)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+    Ad, As, B = dev(s["A_diag"]), dev(s["A_sub"]), dev(s["B"])
+    off = Solver(N, n, d_max=d, precision=prec)
+    off.set_option("shift", 0)
+    with pytest.raises(BDSSError) as e:
+        off.factor_solve(Ad, As, B)
+    assert e.value.status == 2
+    off.close()
+    sol = Solver(N, n, d_max=d, precision=prec)
+    X = sol.factor_solve(Ad, As, B).cpu().numpy()
+    sigma = sol.factor_shift()
+    plain, cg = sol.refine_stats()
+    sol.close()
+    assert sigma > 0 and cg > 0
+    assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], X, s["B"]) <= 1e-14
+    Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
+    # forward error bounded by about kappa u_64 (both solutions are backward stable)
+    assert oracle_mod.forward_error(X, Xo) <= 1e9 * 2.2e-16 * 50
