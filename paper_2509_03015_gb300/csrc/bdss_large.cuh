@@ -46,73 +46,47 @@ struct View {
 // acc[i][j] += sum_k A(r0 + 4 tm + i, k) * B(c0 + 4 tn + j, k) for the 64 x 64
 // output tile at (r0, c0), k over [0, K): "NT" products of two strided views
 // through shared memory (sA, sB: kKc x kTilePad each).  256 threads: thread t
-// owns rows 4 (t / 16) + i and columns 4 (t % 16) + j.
+// owns rows 4 (t / 16) + i and columns 4 (t % 16) + j.  The next k-chunk is
+// loaded into registers (all loads of a chunk issued together) while the
+// current one is multiplied, so global latency overlaps the FMAs.
 template <typename T, typename VA, typename VB>
 __device__ void gemm_nt_tile(T (&acc)[4][4], const VA &A, int r0, const VB &B, int c0, int K, T *sA, T *sB) {
   const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
-  if constexpr (sizeof(T) == 8) {
-    // FP64 (one CTA per SM): the next k-chunk is loaded into registers while
-    // the current one is multiplied, so its global latency overlaps the DFMAs
-    constexpr int kPer = kTile * kKc / kThreads;  // elements per thread and operand
-    T ra[kPer], rb[kPer];
-    auto load = [&](int k0) {
+  constexpr int kPer = kTile * kKc / kThreads;  // elements per thread and operand
+  T ra[kPer], rb[kPer];
+  auto load = [&](int k0) {
 #pragma unroll
-      for (int q = 0; q < kPer; ++q) {
-        const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
-        const bool kin = (k0 + k) < K;
-        ra[q] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
-        rb[q] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
-      }
-    };
-    load(0);
-    for (int k0 = 0; k0 < K; k0 += kKc) {
-#pragma unroll
-      for (int q = 0; q < kPer; ++q) {
-        const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
-        sA[k * kTilePad + m] = ra[q];
-        sB[k * kTilePad + m] = rb[q];
-      }
-      __syncthreads();
-      if (k0 + kKc < K) load(k0 + kKc);
-      const int kc = min(kKc, K - k0);
-      for (int k = 0; k < kc; ++k) {
-        T a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          a[i] = sA[k * kTilePad + 4 * tm + i];
-          b[i] = sB[k * kTilePad + 4 * tn + i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-      }
-      __syncthreads();
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      const bool kin = (k0 + k) < K;
+      ra[q] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
+      rb[q] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
     }
-  } else {
-    for (int k0 = 0; k0 < K; k0 += kKc) {
-      for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
-        const int m = e / kKc, k = e - m * kKc;
-        const bool kin = (k0 + k) < K;
-        sA[k * kTilePad + m] = kin ? (T)A.at(r0 + m, k0 + k) : T(0);
-        sB[k * kTilePad + m] = kin ? (T)B.at(c0 + m, k0 + k) : T(0);
-      }
-      __syncthreads();
-      const int kc = min(kKc, K - k0);
-      for (int k = 0; k < kc; ++k) {
-        T a[4], b[4];
+  };
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += kKc) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          a[i] = sA[k * kTilePad + 4 * tm + i];
-          b[i] = sB[k * kTilePad + 4 * tn + i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-      }
-      __syncthreads();
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      sA[k * kTilePad + m] = ra[q];
+      sB[k * kTilePad + m] = rb[q];
     }
+    __syncthreads();
+    if (k0 + kKc < K) load(k0 + kKc);
+    const int kc = min(kKc, K - k0);
+    for (int k = 0; k < kc; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = sA[k * kTilePad + 4 * tm + i];
+        b[i] = sB[k * kTilePad + 4 * tn + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
   }
 }
 
@@ -120,20 +94,39 @@ __device__ void gemm_nt_tile(T (&acc)[4][4], const VA &A, int r0, const VB &B, i
 // from c0 (right-hand sides).  Thread t owns row t / 4 and columns
 // 4 (t % 4) + j, so every thread works when d <= 16 (the square tile would
 // leave three quarters of its FMAs on zero columns).  sB needs kKc x 17.
+// The next chunk is prefetched into registers as in gemm_nt_tile.
 constexpr int kNarrow = 16;
 template <typename T, typename VA, typename VB>
 __device__ void gemm_nt_narrow(T (&acc)[4], const VA &A, int r0, const VB &B, int c0, int K, T *sA, T *sB) {
   const int tr = threadIdx.x >> 2, tc = threadIdx.x & 3;
-  for (int k0 = 0; k0 < K; k0 += kKc) {
-    for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
-      const int m = e / kKc, k = e - m * kKc;
-      sA[k * kTilePad + m] = (k0 + k) < K ? (T)A.at(r0 + m, k0 + k) : T(0);
+  constexpr int kPa = kTile * kKc / kThreads, kPb = kNarrow * kKc / kThreads;
+  T ra[kPa], rb[kPb];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < kPa; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      ra[q] = (k0 + k) < K ? (T)A.at(r0 + m, k0 + k) : T(0);
     }
-    for (int e = threadIdx.x; e < kNarrow * kKc; e += blockDim.x) {
-      const int m = e / kKc, k = e - m * kKc;
-      sB[k * (kNarrow + 1) + m] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
+#pragma unroll
+    for (int q = 0; q < kPb; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      rb[q] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+#pragma unroll
+    for (int q = 0; q < kPa; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      sA[k * kTilePad + m] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kPb; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      sB[k * (kNarrow + 1) + m] = rb[q];
     }
     __syncthreads();
+    if (k0 + kKc < K) load(k0 + kKc);
     const int kc = min(kKc, K - k0);
     for (int k = 0; k < kc; ++k) {
       const T a = sA[k * kTilePad + tr];
@@ -152,16 +145,34 @@ template <typename T, typename VB>
 __device__ void gemm_tn_narrow(T (&acc)[4], const T *At, long long ld, int M, int r0, const VB &B, int c0, int K,
                                T *sA, T *sB) {
   const int tr = threadIdx.x >> 2, tc = threadIdx.x & 3;
-  for (int k0 = 0; k0 < K; k0 += kKc) {
-    for (int e = threadIdx.x; e < kTile * kKc; e += blockDim.x) {
-      const int k = e / kTile, m = e - k * kTile;
-      sA[k * kTilePad + m] = (k0 + k < K && r0 + m < M) ? ldcg(At + (long long)(k0 + k) * ld + r0 + m) : T(0);
+  constexpr int kPa = kTile * kKc / kThreads, kPb = kNarrow * kKc / kThreads;
+  T ra[kPa], rb[kPb];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < kPa; ++q) {
+      const int e = threadIdx.x + q * kThreads, k = e / kTile, m = e - k * kTile;
+      ra[q] = (k0 + k < K && r0 + m < M) ? ldcg(At + (long long)(k0 + k) * ld + r0 + m) : T(0);
     }
-    for (int e = threadIdx.x; e < kNarrow * kKc; e += blockDim.x) {
-      const int m = e / kKc, k = e - m * kKc;
-      sB[k * (kNarrow + 1) + m] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
+#pragma unroll
+    for (int q = 0; q < kPb; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      rb[q] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+#pragma unroll
+    for (int q = 0; q < kPa; ++q) {
+      const int e = threadIdx.x + q * kThreads, k = e / kTile, m = e - k * kTile;
+      sA[k * kTilePad + m] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kPb; ++q) {
+      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
+      sB[k * (kNarrow + 1) + m] = rb[q];
     }
     __syncthreads();
+    if (k0 + kKc < K) load(k0 + kKc);
     const int kc = min(kKc, K - k0);
     for (int k = 0; k < kc; ++k) {
       const T a = sA[k * kTilePad + tr];
@@ -213,6 +224,7 @@ __device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_
     const int k0 = k * kTile, kb = min(kTile, n - k0);
     const bool first = (k == 0) && src_sym;
     // diagonal tile
+#pragma unroll 4
     for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
       const int r = e / kTile, c = e - r * kTile;
       T v = T(0);
@@ -232,6 +244,7 @@ __device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_
       // reuse the gemm staging area for the panel rows (ib x kb)
       T *sP = sA;  // needs kTile x kTilePad: sA and sB are contiguous 2 * kKc * kTilePad = kTile * kTilePad
       __syncthreads();
+#pragma unroll 4
       for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
         const int r = e / kTile, c = e - r * kTile;
         T v = T(0);
@@ -299,6 +312,7 @@ __device__ void trsv_fwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
         __syncthreads();
       }
     }
+#pragma unroll 4
     for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
       const int r = e / kTile, c = e - r * kTile;
       sT[r * kTilePad + c] = (r < rb && c <= r) ? ldcg(L + (long long)(r0 + r) * n + r0 + c) : T(0);
@@ -336,6 +350,7 @@ __device__ void trsv_bwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
         __syncthreads();
       }
     }
+#pragma unroll 4
     for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
       const int r = e / kTile, c = e - r * kTile;
       sT[r * kTilePad + c] = (r < rb && c <= r) ? ldcg(L + (long long)(r0 + r) * n + r0 + c) : T(0);
@@ -404,6 +419,7 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
   T *work = sV + (size_t)VT * lv;
   const T *E = (l == 0) ? nullptr : a.Eb + (size_t)a.p.off[l] * nn;  // couplings formed at level l-1
   // stage vectors
+#pragma unroll 8
   for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
     const int i = e / nv, cc = e - i * nv, c = c0 + cc;
     T val;
@@ -708,6 +724,7 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
     return;
   }
   trsv_bwd_blocked(a.Ld + (size_t)orig * nn, n, sV, d, work);
+#pragma unroll 4
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
     const int i = e / d, c = e - i * d;
     const T x = sV[(size_t)c * lv + i];
@@ -742,6 +759,7 @@ __device__ bool largeTop(const Args<T> &a, bool factor, double *smem, int *s_fla
   if (d > 0) {
     double *sV = smem;
     double *work = sV + (size_t)d * lv;
+#pragma unroll 4
     for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
       const int i = e / d, c = e - i * d;
       double v;

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def test_chunk_reduce_matches_definition(oracle_mod, Ni, n, d, sides):
     from paper_2509_03015_gb300 import Solver
     s = inputs.random_btd(Ni + 2, n, d, seed=Ni * n)
-    Ad, As, B = s["A_diag"][1:-1], s["A_sub"][1:-2], s["B"][1:-1]
+    Ad, As, B = s["A_diag"][1:-1], s["A_sub"][1:-1], s["B"][1:-1]
     A_left = s["A_sub"][0] if sides in ("both", "left") else None
     A_right = s["A_sub"][-1] if sides in ("both", "right") else None
     elim, back, _ = _cpu_ops(oracle_mod)
