@@ -348,9 +348,12 @@ def other_workloads(dev, stream, world, max_over_ranks, args, oracle_job=None):
     Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
     X = torch.empty_like(B)
     sol = Solver(cfg["N"], cfg["n"], d_max=cfg["d"], stream=stream)
+    # the crossover N_* (Sec. 3.3), autotuned on this system
+    nstar, nstar_ms = sol.tune_nstar(Ad, As, B, reps=10)
     sol.factor_solve(Ad, As, B, X)
     ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 20, stream, max_over_ranks)
-    res[name] = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms,
+    res[name] = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms, "nstar": nstar,
+                 "nstar_candidates_ms": nstar_ms,
                  "note": "one call = one persistent launch + status read-back"}
     sol.close()
     # -- mixed precision at n = 256 --------------------------------------------
@@ -425,9 +428,55 @@ def other_workloads(dev, stream, world, max_over_ranks, args, oracle_job=None):
     fwd_bwd()
     ms = _timed(fwd_bwd, reps, stream, max_over_ranks)
     res[name] = {"value": world * 1e3 / ms, "unit": "systems/s (forward + backward)", "ms_per_step": ms}
+    # -- mixed precision beyond 1/u_32 ----------------------------------------------------
+    res["refinement-krylov-laplace-N32768-n4-d2"] = krylov_leg(dev, stream, world, max_over_ranks)
+    res["shifted-factor-illcond-N4096-n32-d2"] = shifted_leg(dev, stream, world, max_over_ranks)
     # -- Kalman-smoother assembly on the device ---------------------------------------
     res["kalman-assembly-N16384-n64-m32"] = kalman_assembly(dev, stream, world, max_over_ranks, reps)
     return res
+
+
+def krylov_leg(dev, stream, world, max_over_ranks, N=32768, n=4, d=2):
+    """FP32 factors + refinement on the block 1-D Laplacian with kappa ~ 7.5e8
+    (inputs.laplace_btd): plain refinement stalls and the default mode
+    continues with FP64 CG preconditioned by the FP32 factors."""
+    import torch
+
+    from paper_2509_03015_gb300 import Solver
+    s = inputs.laplace_btd(N, n, d, seed=1)
+    Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
+    X = torch.empty_like(B)
+    sol = Solver(N, n, d_max=d, precision="fp32_ir", stream=stream)
+    sol.factor_solve(Ad, As, B, X)
+    ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 2, stream, max_over_ranks)
+    plain, cg = sol.refine_stats()
+    out = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms, "refine_plain_steps": plain,
+           "refine_cg_iters": cg, "backward_err": sol.last_info.backward_err, "kappa_approx": 0.6 * N * N}
+    sol.close()
+    return out
+
+
+def shifted_leg(dev, stream, world, max_over_ranks, N=4096, n=32, d=2):
+    """kappa ~ 1e9 with blocks whose FP32 Cholesky fails (inputs.illcond_btd):
+    the shifted FP32 factorisation A + sigma diag(A) and FP64 CG refinement."""
+    import torch
+
+    from paper_2509_03015_gb300 import Solver
+    s = inputs.illcond_btd(N, n, d, seed=2, kappa=1e9)
+    Ad, As, B = (torch.from_numpy(s[k]).to(dev) for k in ("A_diag", "A_sub", "B"))
+    X = torch.empty_like(B)
+    sol = Solver(N, n, d_max=d, precision="fp32_ir", stream=stream)
+    sol.factor_solve(Ad, As, B, X)
+    ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 2, stream, max_over_ranks)
+    plain, cg = sol.refine_stats()
+    out = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms, "shift_sigma": sol.factor_shift(),
+           "refine_plain_steps": plain, "refine_cg_iters": cg, "backward_err": sol.last_info.backward_err}
+    fp64 = Solver(N, n, d_max=d, stream=stream)
+    fp64.factor_solve(Ad, As, B, X)
+    out["fp64_ms"] = _timed(lambda: fp64.factor_solve(Ad, As, B, X), 2, stream, max_over_ranks)
+    fp64.close()
+    sol.close()
+    return out
 
 
 def kalman_assembly(dev, stream, world, max_over_ranks, reps, N=16384, n=64, m=32):

@@ -117,6 +117,13 @@ typedef enum {
                                    first use; at most 4 cycles, each restarted from the
                                    true FP64 residual */
   BDSS_OPT_MAX_KRYLOV_ITERS = 8, /* mixed precision: CG iterations per cycle (default 300) */
+  BDSS_OPT_NSTAR = 12,          /* the crossover N_* of Sec. 3.3 (default 1): the reduction
+                                   stops at the first level with at most N_* blocks, which
+                                   one CTA then factors and solves by the serial block-
+                                   Cholesky sweep (Algorithms 1 and 2 with K = 1), in FP64.
+                                   1 <= N_* <= 64; values above 1 are offered for FP64
+                                   handles with n <= 64 (else BDSS_ERR_UNSUPPORTED).
+                                   Setting it discards the stored factors */
   BDSS_OPT_SHIFT = 11,          /* mixed precision: 1 (default) = when an FP32 pivot fails
                                    (kappa(A) beyond about 1/u_32), factor A + sigma diag(A)
                                    instead, sigma = 2^-20 growing 16x per failure up to

@@ -66,6 +66,7 @@ struct bdss_ctx {
   double *kr_part = nullptr, *kr_sc = nullptr;
   int last_plain = 0, last_cg = 0;  // refinement steps of the last solve
   // mixed precision: shifted factorisation when an FP32 pivot fails
+  int nstar = 1;            // crossover N_*: top levels of up to nstar blocks are swept serially
   int shift_on = 1;
   double shift_used = 0.0;   // relative diagonal shift of the stored factors
   double *Ashift = nullptr;  // shifted copy of A_diag (allocated on first use)
@@ -194,19 +195,23 @@ static void kt_end(bdss_ctx *h, int launches) {
 
 static bool is_mixed(const bdss_ctx *h) { return h->prec != BDSS_FP64; }
 
-static void make_plan(Plan &p, int64_t N, int n) {
+// Level sizes N_{l+1} = ceil(N_l / 2) down to one block (their coupling
+// regions are laid out for every level); the reduction stops at the first
+// level with at most nstar blocks, which the top sweep then factors.
+static void make_plan(Plan &p, int64_t N, int n, int nstar = 1) {
   memset(&p, 0, sizeof(p));
   p.N = N;
   p.n = n;
   p.Nl[0] = N;
   p.off[0] = 0;
-  int l = 0;
+  int l = 0, stop = -1;
   while (p.Nl[l] > 1) {
+    if (stop < 0 && p.Nl[l] <= nstar) stop = l;
     p.Nl[l + 1] = (p.Nl[l] + 1) / 2;
     p.off[l + 1] = p.off[l] + (p.Nl[l] - 1);
     ++l;
   }
-  p.L = l;
+  p.L = stop >= 0 ? stop : l;
 }
 
 static int grid_for(const bdss_ctx *h, long long items) {
@@ -458,7 +463,10 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
   bool ok = ws_alloc(h, &h->Ld, (size_t)N * nn * esz);
   ok = ok && ws_alloc(h, &h->Wb, slots * nn * esz);
   if (h->large) ok = ok && ws_alloc(h, &h->Eb, slots * nn * esz);
-  ok = ok && ws_alloc(h, (void **)&h->Ltop, nn * sizeof(double));
+  // the top factors: one block, or (blocks up to n = 64) the L_j, C_j and
+  // y_j of a serial top sweep of up to kNStarMax blocks
+  const size_t top_words = h->large ? nn : (size_t)kNStarMax * (2 * nn + (size_t)n * d_max);
+  ok = ok && ws_alloc(h, (void **)&h->Ltop, top_words * sizeof(double));
   ok = ok && ws_alloc(h, (void **)&h->partial, kLogdetGrid * sizeof(double));
   ok = ok && ws_alloc(h, (void **)&h->dst, sizeof(DevStatus));
   ok = ok && !inject_alloc_failure() && cudaMallocHost((void **)&h->hst, sizeof(DevStatus)) == cudaSuccess;
@@ -542,6 +550,16 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
       if (value < 1 || value > 100000) return BDSS_ERR_INVALID_ARG;
       h->max_krylov = (int)value;
       return BDSS_OK;
+    case BDSS_OPT_NSTAR: {
+      if (value < 1 || value > kNStarMax) return BDSS_ERR_INVALID_ARG;
+      // the serial sweep stages two blocks and the vectors in FP64
+      const size_t need = ((size_t)(2 * h->n + h->d_max) * ldstride(h->n) + 8) * sizeof(double);
+      if (value > 1 && (h->large || is_mixed(h) || need > h->smem)) return BDSS_ERR_UNSUPPORTED;
+      h->nstar = (int)value;
+      make_plan(h->plan, h->N, h->n, h->nstar);
+      h->factored = false;
+      return BDSS_OK;
+    }
     case BDSS_OPT_SHIFT:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
       h->shift_on = (int)value;
@@ -987,8 +1005,10 @@ bdss_status bdss_logdet(bdss_handle h, double *out) {
   int grid = (int)((total + kThreads - 1) / kThreads);
   if (grid > kLogdetGrid) grid = kLogdetGrid;
   cudaError_t e = is_mixed(h)
-                      ? launch_logdet<float>(h->N, h->n, (const float *)h->Ld, h->Ltop, h->partial, grid, h->stream)
-                      : launch_logdet<double>(h->N, h->n, (const double *)h->Ld, h->Ltop, h->partial, grid, h->stream);
+                      ? launch_logdet<float>(h->N, h->n, h->plan.L, (const float *)h->Ld, h->Ltop, h->partial, grid,
+                                             h->stream)
+                      : launch_logdet<double>(h->N, h->n, h->plan.L, (const double *)h->Ld, h->Ltop, h->partial,
+                                              grid, h->stream);
   double part[kLogdetGrid];
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(part, h->partial, grid * sizeof(double), cudaMemcpyDeviceToHost, h->stream);

@@ -1117,10 +1117,131 @@ __device__ void phaseB(const Args<T> &a, int l, long long k, bool factor, T *sme
 }
 
 // ---------------------------------------------------------------------------
-// Top block (the base case of Algorithms 4 and 7 with N_* = 1), always FP64.
+// Serial top sweep: the recursion stops at the first level with at most N_*
+// blocks (Sec. 3.3: below the crossover N_* the serial block-Cholesky sweep
+// is used) and the M blocks of that level are factored by Algorithm 1 with
+// K = 1 and solved by Algorithm 2 with K = 1, in FP64 by one CTA:
+//   D_j' = D_j - C_{j-1} C_{j-1}^T,  L_j = chol(D_j'),  C_j = E_j L_j^{-T},
+//   y_j = L_j^{-1} (b_j - C_{j-1} y_{j-1}),  x_j = L_j^{-T} (y_j - C_j^T x_{j+1}),
+// with E_j = A_{j+1,j} of that level.  Ltop holds L_j at j n^2, C_j at
+// (kNStarMax + j) n^2 and y_j / x_j at 2 kNStarMax n^2 + j n d (doubles).
+// Shared memory: (2 n + d) ldstride(n) doubles.
+// ---------------------------------------------------------------------------
+constexpr int kNStarMax = 64;  // largest N_* (top blocks of the serial sweep)
+
+template <typename T>
+__device__ bool top_sweep(const Args<T> &a, bool factor, double *smem, int *s_flag) {
+  const int n = a.p.n, ld = ldstride(n), d = a.d, L = a.p.L;
+  const int M = (int)a.p.Nl[L];
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  double *sL = smem;                     // L_j (lower, reciprocal diagonal)
+  double *sC = sL + (size_t)n * ld;      // rows of E_j, then of C_j
+  double *sB = sC + (size_t)n * ld;      // d vectors
+  double *LC = a.Ltop + (size_t)kNStarMax * nn;
+  double *Ys = a.Ltop + (size_t)2 * kNStarMax * nn;
+  const T *E = (L == 0) ? nullptr : a.Wb + (size_t)a.p.off[L] * nn;
+  for (int j = 0; j < M; ++j) {
+    const long long orig = (long long)j << L;
+    if (factor) {
+      if (L == 0) stage_sym_lower(sL, ld, a.A_diag + orig * nn, n);
+      else stage_lower(sL, ld, a.Ld + orig * nn, n);
+      __syncthreads();
+      if (j > 0) {  // D_j -= C_{j-1} C_{j-1}^T (lower triangle)
+        const double *Cp = LC + (size_t)(j - 1) * nn;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+          const int r = e / n, c = e - r * n;
+          if (c > r) continue;
+          double acc = 0.0;
+          for (int k = 0; k < n; ++k) acc = fma(ldcg(Cp + (size_t)r * n + k), ldcg(Cp + (size_t)c * n + k), acc);
+          sL[r * ld + c] -= acc;
+        }
+        __syncthreads();
+      }
+      if (chol_staged(sL, ld, n, s_flag)) {
+        if (threadIdx.x == 0) set_status(a.st, kStNotSPD, L, orig);
+        __syncthreads();
+        return false;
+      }
+      double *Lj = a.Ltop + (size_t)j * nn;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        Lj[e] = (c <= r) ? sL[r * ld + c] : 0.0;
+      }
+      if (j + 1 < M) {  // C_j = E_j L_j^{-T}: row r of C_j solves L_j c = E_j[r]^T
+        if (L == 0) stage_row_range(sC, ld, a.A_sub + (size_t)j * nn, n, 0, n);
+        else stage_row_range(sC, ld, E + (size_t)j * nn, n, 0, n);
+        __syncthreads();
+        trsv_fwd_cta(sL, ld, n, sC, n);
+        __syncthreads();
+        double *Cj = LC + (size_t)j * nn;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Cj[e] = sC[(e / n) * ld + e % n];
+      }
+    } else {
+      stage_lower(sL, ld, a.Ltop + (size_t)j * nn, n);
+    }
+    if (d > 0) {
+      const size_t bo = (size_t)orig * nd;
+      if (L == 0 && a.B64) stage_cols(sB, ld, a.B64 + bo, n, d);
+      else if (L == 0 && a.Bt) stage_cols(sB, ld, a.Bt + bo, n, d);
+      else stage_cols(sB, ld, a.Y + bo, n, d);
+      __syncthreads();
+      if (j > 0) {  // b_j -= C_{j-1} y_{j-1}
+        const double *Cp = LC + (size_t)(j - 1) * nn, *yp = Ys + (size_t)(j - 1) * nd;
+        for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+          const int c = e / n, i = e - c * n;
+          double acc = 0.0;
+          for (int k = 0; k < n; ++k) acc = fma(ldcg(Cp + (size_t)i * n + k), ldcg(yp + (size_t)k * d + c), acc);
+          sB[c * ld + i] -= acc;
+        }
+        __syncthreads();
+      }
+      trsv_fwd_cta(sL, ld, n, sB, d);
+      __syncthreads();
+      double *yj = Ys + (size_t)j * nd;
+      for (int e = threadIdx.x; e < n * d; e += blockDim.x) yj[e] = sB[(e % d) * ld + e / d];
+    }
+    __syncthreads();
+  }
+  if (d > 0) {
+    for (int j = M - 1; j >= 0; --j) {  // x_j = L_j^{-T} (y_j - C_j^T x_{j+1})
+      const long long orig = (long long)j << L;
+      stage_lower(sL, ld, a.Ltop + (size_t)j * nn, n);
+      double *yj = Ys + (size_t)j * nd;
+      for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+        const int c = e / n, i = e - c * n;
+        double v = ldcg(yj + (size_t)i * d + c);
+        if (j + 1 < M) {
+          const double *Cj = LC + (size_t)j * nn, *xn = Ys + (size_t)(j + 1) * nd;
+          for (int k = 0; k < n; ++k) v = fma(-ldcg(Cj + (size_t)k * n + i), ldcg(xn + (size_t)k * d + c), v);
+        }
+        sB[c * ld + i] = v;
+      }
+      __syncthreads();
+      trsv_bwd_cta(sL, ld, n, sB, d);
+      __syncthreads();
+      for (int e = threadIdx.x; e < n * d; e += blockDim.x) {
+        const int i = e / d, c = e - i * d;
+        const double x = sB[c * ld + i];
+        yj[e] = x;
+        a.Y[(size_t)orig * nd + e] = (T)x;
+        if (a.X64) {
+          double *xo = a.X64 + (size_t)orig * nd + e;
+          *xo = a.x_accumulate ? *xo + x : x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Top block (the base case of Algorithms 4 and 7 with N_* = 1), always FP64;
+// a top level of several blocks (N_* > 1) goes to the serial sweep.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ bool top_block(const Args<T> &a, bool factor, double *smem, int *s_flag) {
+  if (a.p.Nl[a.p.L] > 1) return top_sweep(a, factor, smem, s_flag);
   const int n = a.p.n, ld = ldstride(n), d = a.d, L = a.p.L;
   double *sL = smem;
   double *sB = sL + (size_t)n * ld;

@@ -41,7 +41,7 @@ constexpr int kFrac = 59;                 // fraction bits of the fixed-point di
 constexpr int kDiag = 2 * kS - 1;         // accumulators (diagonals p + q)
 constexpr int kM = 128;                   // output rows of a tile (TMEM lanes)
 constexpr int kN = kS * kEmuDp;           // 160: X slices stacked as the B operand
-constexpr int kRowsPerCta = 16;           // operator rows per slicing CTA
+constexpr int kRowsPerCta = 8;            // operator rows per slicing CTA
 constexpr int kAStages = 8;
 constexpr int kXStages = 2;
 constexpr int kATile = kM * kEmuKc * 2;   // 16384 bytes
@@ -65,24 +65,38 @@ __device__ __forceinline__ long long emu_fixed(double v, int E) {
   return b < 0 ? -q : q;
 }
 
-// Signed base-64 digits of q (|q| < 2^59): q = sum_p d[p] 64^(9-p),
-// d[p] in [-32, 31] for p >= 1 and |d[0]| <= 32.
-__device__ __forceinline__ void emu_digits(long long q, int (&d)[kS]) {
-#pragma unroll
-  for (int p = kS - 1; p > 0; --p) {
-    const int r = (int)((q + 32) & 63) - 32;
-    d[p] = r;
-    q = (q - r) >> 6;
-  }
-  d[0] = (int)q;
+// Signed base-64 digits of q (|q| < 2^59): q = sum_p d[p] 64^(9-p) with
+// d[p] in [-32, 31] for p >= 1 and |d[0]| <= 32.  With u = q + 32 sum_p 64^p
+// every digit of u in plain base 64 is d[p] + 32 (the bias absorbs the
+// borrows), so the digits come without a carry chain: the biased digit p is
+// (u >> 6 (9 - p)) & 63, and the top one u >> 54 (at most 64).
+constexpr long long kEmuBias = 32LL * 18300341342965825LL;  // 32 (64^10 - 1) / 63
+__device__ __forceinline__ int emu_biased_digit(unsigned long long u, int p) {
+  return p == 0 ? (int)(u >> 54) : (int)((u >> (6 * (kS - 1 - p))) & 63);
 }
 
-// BF16 bits of a small integer (|d| <= 64): 2^23 + d + 64 is exact in FP32,
-// subtracting 2^23 + 64 leaves d exactly, and d needs at most 7 significant
-// bits, so the upper half of its FP32 pattern is its BF16 pattern.
-__device__ __forceinline__ unsigned short emu_bf16(int d) {
-  const float f = __int_as_float(0x4B000000 + d + 64) - 8388672.0f;
-  return (unsigned short)(__float_as_uint(f) >> 16);
+// BF16 bits of the integer b - 32 for a biased digit 0 <= b <= 64: 2^23 + b
+// is exact in FP32, subtracting 2^23 + 32 leaves b - 32 exactly, and
+// |b - 32| <= 32 needs at most 6 significant bits, so the upper half of its
+// FP32 pattern is its BF16 pattern.
+__device__ __forceinline__ unsigned emu_bf16_biased(int b) {
+  const float f = __int_as_float(0x4B000000 + b) - 8388640.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// Ten digit planes of four consecutive entries: writes 8 bytes (four BF16)
+// per plane at dst + p * plane_stride (elements).
+__device__ __forceinline__ void emu_store_quad(const double (&v)[4], int E, unsigned short *dst,
+                                               size_t plane_stride) {
+  unsigned long long u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u[j] = (unsigned long long)(emu_fixed(v[j], E) + kEmuBias);
+#pragma unroll
+  for (int p = 0; p < kS; ++p) {
+    const unsigned lo = emu_bf16_biased(emu_biased_digit(u[0], p)) | (emu_bf16_biased(emu_biased_digit(u[1], p)) << 16);
+    const unsigned hi = emu_bf16_biased(emu_biased_digit(u[2], p)) | (emu_bf16_biased(emu_biased_digit(u[3], p)) << 16);
+    *reinterpret_cast<uint2 *>(dst + (size_t)p * plane_stride) = make_uint2(lo, hi);
+  }
 }
 
 // Exponent E with max |x| < 2^E from the bits of max |x| (a zero maximum:
@@ -93,7 +107,7 @@ __device__ __forceinline__ int emu_exp(unsigned long long maxbits) {
 }
 
 // ---------------------------------------------------------------------------
-// Operator slices: CTA (block row i, rows r0 .. r0 + 15).
+// Operator slices: CTA (block row i, rows r0 .. r0 + kRowsPerCta - 1).
 // Aslc[((i S + p) n + r) 3np + g np + k] = digit p of entry k of block g of
 // operator row (i, r); g = 0: A_{i,i-1}, 1: sym(A_ii), 2: A_{i,i+1} =
 // A_{i+1,i}^T; zero for absent blocks and k >= n.
@@ -112,7 +126,8 @@ __global__ void __launch_bounds__(256) k_emu_slice_operator(long long N, int n, 
   const size_t nn = (size_t)n * n;
   const bool hasL = i > 0, hasR = i + 1 < N;
   double *T0 = T, *T1 = T + (size_t)kRowsPerCta * n, *T2 = T + (size_t)2 * kRowsPerCta * n;
-  // rows of A_{i,i-1} and A_ii
+  // rows of A_{i,i-1} and A_ii (unrolled so that several loads are in flight)
+#pragma unroll 4
   for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
     const int rr = e / n, k = e - rr * n;
     T0[e] = hasL ? __ldg(A_sub + (size_t)(i - 1) * nn + (size_t)(r0 + rr) * n + k) : 0.0;
@@ -120,6 +135,7 @@ __global__ void __launch_bounds__(256) k_emu_slice_operator(long long N, int n, 
   }
   __syncthreads();
   // columns r0 .. r0 + R - 1 of A_ii (symmetrise) and of A_{i+1,i}
+#pragma unroll 4
   for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
     const int k = e / R, rr = e - k * R;
     const double at = __ldg(A_diag + (size_t)i * nn + (size_t)k * n + r0 + rr);
@@ -159,16 +175,16 @@ __global__ void __launch_bounds__(256) k_emu_slice_operator(long long N, int n, 
     for (int w = 0; w < 8; ++w) m = fmaxf(m, sNorm[w]);
     atomicMax(&st->nrm[2], (unsigned long long)__double_as_longlong((double)m));
   }
-  // digits: consecutive threads take consecutive k of one (row, block)
-  const int K3 = 3 * np;
-  for (int e = threadIdx.x; e < R * K3; e += blockDim.x) {
-    const int rr = e / K3, kk = e - rr * K3, g = kk / np, k = kk - g * np;
-    const double v = k < n ? T[(size_t)g * kRowsPerCta * n + (size_t)rr * n + k] : 0.0;
-    int dg[kS];
-    emu_digits(emu_fixed(v, sE[rr]), dg);
+  // digits: consecutive threads take consecutive quads of k of one (row,
+  // block); np is a multiple of 64, so a quad never straddles two blocks
+  const int K3 = 3 * np, Q3 = K3 / 4;
+  for (int e = threadIdx.x; e < R * Q3; e += blockDim.x) {
+    const int rr = e / Q3, kk = 4 * (e - rr * Q3), g = kk / np, k = kk - g * np;
+    const double *src = T + (size_t)g * kRowsPerCta * n + (size_t)rr * n;
+    double v[4];
 #pragma unroll
-    for (int p = 0; p < kS; ++p)
-      Aslc[(((size_t)i * kS + p) * n + r0 + rr) * K3 + kk] = emu_bf16(dg[p]);
+    for (int j = 0; j < 4; ++j) v[j] = (k + j < n) ? src[k + j] : 0.0;
+    emu_store_quad(v, sE[rr], Aslc + ((size_t)i * kS * n + r0 + rr) * K3 + kk, (size_t)n * K3);
   }
 }
 
@@ -206,13 +222,13 @@ __global__ void __launch_bounds__(256) k_emu_slice_x(long long N, int n, int np,
   }
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) sX[e] = __ldg(X + (size_t)j * n * d + e);
   __syncthreads();
-  for (int e = threadIdx.x; e < kEmuDp * np; e += blockDim.x) {
-    const int c = e / np, k = e - c * np;
-    const double v = (c < d && k < n) ? sX[k * d + c] : 0.0;
-    int dg[kS];
-    emu_digits(emu_fixed(v, sF[c]), dg);
+  const int nq = np / 4;
+  for (int e = threadIdx.x; e < kEmuDp * nq; e += blockDim.x) {
+    const int c = e / nq, k = 4 * (e - c * nq);
+    double v[4];
 #pragma unroll
-    for (int q = 0; q < kS; ++q) Xslc[(((size_t)j * kS + q) * kEmuDp + c) * np + k] = emu_bf16(dg[q]);
+    for (int t = 0; t < 4; ++t) v[t] = (c < d && k + t < n) ? sX[(k + t) * d + c] : 0.0;
+    emu_store_quad(v, sF[c], Xslc + ((size_t)j * kS * kEmuDp + c) * np + k, (size_t)kEmuDp * np);
   }
 }
 

@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(long long N, int n, int d
 // log det: sum over eliminated blocks (every original block i >= 1) of
 // -2 sum_k log(1/L_kk) plus the top block's; reduced per CTA into out[blockIdx].
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_logdet(long long N, int n, const T *Ld, const double *Ltop,
-                                                     double *partial) {
+__global__ void __launch_bounds__(kThreads) k_logdet(long long N, int n, int Ltop_level, const T *Ld,
+                                                     const double *Ltop, double *partial) {
   __shared__ double red[kThreads];
   double s = 0.0;
   const size_t nn = (size_t)n * n;
@@ -211,7 +211,10 @@ __global__ void __launch_bounds__(kThreads) k_logdet(long long N, int n, const T
        t += (long long)gridDim.x * blockDim.x) {
     const long long i = t / n;
     const int k = (int)(t - i * n);
-    const double rd = (i == 0) ? Ltop[k * n + k] : (double)Ld[i * nn + (size_t)k * n + k];
+    // blocks of the top level (positions j 2^L) were factored into Ltop
+    const bool top = (i & ((1LL << Ltop_level) - 1)) == 0;
+    const double rd = top ? Ltop[(size_t)(i >> Ltop_level) * nn + (size_t)k * n + k]
+                          : (double)Ld[i * nn + (size_t)k * n + k];
     s -= 2.0 * log(rd);
   }
   red[threadIdx.x] = s;
@@ -368,9 +371,9 @@ cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, con
 
 
 template <typename T>
-cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, double *partial, int grid,
+cudaError_t launch_logdet(long long N, int n, int Ltop_level, const T *Ld, const double *Ltop, double *partial, int grid,
                           cudaStream_t s) {
-  k_logdet<T><<<grid, kThreads, 0, s>>>(N, n, Ld, Ltop, partial);
+  k_logdet<T><<<grid, kThreads, 0, s>>>(N, n, Ltop_level, Ld, Ltop, partial);
   return cudaGetLastError();
 }
 
@@ -383,7 +386,7 @@ cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, d
   template cudaError_t launch_phaseB<T>(const Args<T> &, int, int, int, size_t, cudaStream_t);                \
   template cudaError_t launch_top<T>(const Args<T> &, int, size_t, cudaStream_t);                             \
   template cudaError_t launch_phaseC<T>(const Args<T> &, int, int, size_t, cudaStream_t);                     \
-  template cudaError_t launch_logdet<T>(long long, int, const T *, const double *, double *, int, cudaStream_t);
+  template cudaError_t launch_logdet<T>(long long, int, int, const T *, const double *, double *, int, cudaStream_t);
 
 BDSS_INSTANTIATE(double)
 BDSS_INSTANTIATE(float)

@@ -21,9 +21,9 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
     for (long long m = rank; m < nE; m += gridDim.x)
       if (!largeA1(a, l, 2 * m + 1, smem, s_flag)) return false;
   } else if (sub == kSubA2 && !factor && a.Li) {
-    // solve pass with the stored inverses: row tiles of y_j = L_j^{-1} b_j
-    const int nt = ntiles(n);
-    for (long long t = rank; t < nE * nt; t += gridDim.x) largeA2_inv(a, l, 2 * (t / nt) + 1, (int)(t % nt), smem);
+    // solve pass with the stored inverses: y_j = L_j^{-1} b_j, a thread per row
+    if constexpr (sizeof(T) == 4)
+      for (long long m = rank; m < nE; m += gridDim.x) largeA2_rows(a, l, 2 * m + 1, smem);
   } else if (sub == kSubA2) {
     const int VT = vec_tile(sizeof(T));
     const int nvt = (largeA2_slots(a, factor) + VT - 1) / VT;
@@ -49,9 +49,21 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
         return true;
       }
     }
+    if constexpr (sizeof(T) == 4) {
+      if (!factor) {  // solve pass: the separator RHS updates, a thread per row
+        for (long long k = rank; k < nS; k += gridDim.x) largeB_rows(a, l, k, smem);
+        return true;
+      }
+    }
     const int nTB = largeB_tiles(n, factor, d);
     for (long long t = rank; t < nS * nTB; t += gridDim.x) largeB(a, l, t / nTB, (int)(t % nTB), factor, smem);
   } else {
+    if constexpr (sizeof(T) == 4) {
+      if (a.Li) {  // with the stored inverses, a thread per row
+        for (long long m = rank; m < nE; m += gridDim.x) largeC_rows(a, l, 2 * m + 1, smem);
+        return true;
+      }
+    }
     for (long long m = rank; m < nE; m += gridDim.x) largeC(a, l, 2 * m + 1, smem);
   }
   return true;
@@ -298,11 +310,12 @@ long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int 
   const long long Nl = p.Nl[l], nE = Nl / 2, nS = (Nl + 1) / 2;
   if (sub == kSubA1 || sub == kSubC) return nE;
   if (sub == kSubA2) {
-    if (!factor && inv) return nE * ntiles(p.n);
+    if (!factor && inv) return nE;
     const int VT = vec_tile(esz);
     return nE * (((factor ? (inv ? 3 : 2) * p.n : 0) + d + VT - 1) / VT);
   }
   if (tf32 && factor) return nS * (largeB_tc_tiles(p.n) + largeB_tiles(p.n, false, d));
+  if (!factor && esz == 4) return nS;  // a thread per row (largeB_rows)
   return nS * largeB_tiles(p.n, factor != 0, d);
 }
 

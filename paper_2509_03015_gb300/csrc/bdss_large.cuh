@@ -137,52 +137,6 @@ __device__ void gemm_nt_narrow(T (&acc)[4], const VA &A, int r0, const VB &B, in
   }
 }
 
-// The narrow product with the left operand given transposed, row-major in
-// global memory: acc[j] += sum_k At[k * ld + r0 + tr] B(c0 + 4 tc + j, k) for
-// rows r0 + tr < M (zero beyond M or K).  The staging reads rows of At, so
-// its loads are coalesced (the products L^{-T} t of the downward pass).
-template <typename T, typename VB>
-__device__ void gemm_tn_narrow(T (&acc)[4], const T *At, long long ld, int M, int r0, const VB &B, int c0, int K,
-                               T *sA, T *sB) {
-  const int tr = threadIdx.x >> 2, tc = threadIdx.x & 3;
-  constexpr int kPa = kTile * kKc / kThreads, kPb = kNarrow * kKc / kThreads;
-  T ra[kPa], rb[kPb];
-  auto load = [&](int k0) {
-#pragma unroll
-    for (int q = 0; q < kPa; ++q) {
-      const int e = threadIdx.x + q * kThreads, k = e / kTile, m = e - k * kTile;
-      ra[q] = (k0 + k < K && r0 + m < M) ? ldcg(At + (long long)(k0 + k) * ld + r0 + m) : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < kPb; ++q) {
-      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
-      rb[q] = (k0 + k) < K ? (T)B.at(c0 + m, k0 + k) : T(0);
-    }
-  };
-  load(0);
-  for (int k0 = 0; k0 < K; k0 += kKc) {
-#pragma unroll
-    for (int q = 0; q < kPa; ++q) {
-      const int e = threadIdx.x + q * kThreads, k = e / kTile, m = e - k * kTile;
-      sA[k * kTilePad + m] = ra[q];
-    }
-#pragma unroll
-    for (int q = 0; q < kPb; ++q) {
-      const int e = threadIdx.x + q * kThreads, m = e / kKc, k = e - m * kKc;
-      sB[k * (kNarrow + 1) + m] = rb[q];
-    }
-    __syncthreads();
-    if (k0 + kKc < K) load(k0 + kKc);
-    const int kc = min(kKc, K - k0);
-    for (int k = 0; k < kc; ++k) {
-      const T a = sA[k * kTilePad + tr];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fma(a, sB[k * (kNarrow + 1) + 4 * tc + j], acc[j]);
-    }
-    __syncthreads();
-  }
-}
-
 // Shared memory (in elements of FP64) of the FP64 top block: d solution
 // vectors plus the tile work area (it never stages coupling vectors).
 __host__ __device__ inline size_t smem_large_top(int n, int d) {
@@ -469,37 +423,6 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
   __syncthreads();
 }
 
-// Solve pass with the stored inverses: row tile R of y_j = L_j^{-1} b_j (rows
-// 64 R .. 64 R + 63, all RHS columns) into Yt; L^{-1} is lower triangular,
-// so the product stops at column 64 R + 63.
-template <typename T>
-__device__ void largeA2_inv(const Args<T> &a, int l, long long j, int R, T *smem) {
-  const int n = a.p.n, d = a.d;
-  const long long orig = j << l;
-  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
-  T *sA = smem, *sB = sA + kKc * kTilePad;
-  const int r0 = R * kTile, K = min(n, r0 + kTile);
-  const View<T> Lr{a.Li + (size_t)orig * nn, n, 1, n, n};  // (r, k) -> L^{-1}[r][k]
-  for (int c0 = 0; c0 < d; c0 += kNarrow) {
-    T acc[4] = {};
-    // b_j as the right operand: (c, k) -> b[k][c]
-    if (l == 0 && a.B64) {
-      const View<double> Bv{a.B64 + (size_t)orig * nd + c0, 1, d, d - c0, n};
-      gemm_nt_narrow(acc, Lr, r0, Bv, 0, K, sA, sB);
-    } else {
-      const T *src = (l == 0 && a.Bt) ? a.Bt : a.Y;
-      const View<T> Bv{src + (size_t)orig * nd + c0, 1, d, d - c0, n};
-      gemm_nt_narrow(acc, Lr, r0, Bv, 0, K, sA, sB);
-    }
-    const int r = r0 + (threadIdx.x >> 2);
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int c = c0 + 4 * (threadIdx.x & 3) + jj;
-      if (r < n && c < d) a.Yt[(size_t)orig * nd + (size_t)r * d + c] = acc[jj];
-    }
-  }
-}
-
 // Tiles of a separator's phase-B work.
 __host__ __device__ inline int largeB_tiles(int n, bool factor, int d) {
   const int nt = ntiles(n);
@@ -659,6 +582,150 @@ __device__ inline bool largeB_tc(const Args<float> &a, int l, long long k, int t
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Solve passes with the stored inverses (FP32 tiled path), one thread per
+// output row: each product is an n x n matrix times up to 16 vectors that
+// sit in shared memory as sV[k * 16 + c].  Thread r streams row r of the
+// matrix (kTrans = false: P[r ld + k], float4 loads when aligned) or column r
+// (kTrans = true: P[k ld + r], coalesced across the warp), with no barrier
+// inside the product, so that the loads of a whole block are in flight
+// together.
+// ---------------------------------------------------------------------------
+constexpr int kRowCols = 16;
+
+template <bool kTrans>
+__device__ __forceinline__ void rowprod16(float (&acc)[kRowCols], const float *P, int ld, int r, int k0, int k1,
+                                          const float *sV) {
+  int k = k0;
+  if (!kTrans && ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0)) {
+    for (; k < k1 && (k & 3); ++k) {
+      const float a = ldcg(P + (size_t)r * ld + k);
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c) acc[c] = fma(a, sV[k * kRowCols + c], acc[c]);
+    }
+    for (; k + 4 <= k1; k += 4) {
+      const float4 a4 = __ldcg(reinterpret_cast<const float4 *>(P + (size_t)r * ld + k));
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < kRowCols; ++c) acc[c] = fma(av[q], sV[(k + q) * kRowCols + c], acc[c]);
+    }
+  }
+#pragma unroll 4
+  for (; k < k1; ++k) {
+    const float a = kTrans ? ldcg(P + (size_t)k * ld + r) : ldcg(P + (size_t)r * ld + k);
+#pragma unroll
+    for (int c = 0; c < kRowCols; ++c) acc[c] = fma(a, sV[k * kRowCols + c], acc[c]);
+  }
+}
+
+// sV[k * 16 + c] = src[k * d + c0 + c] (k < n, c < 16; zero past column d).
+template <typename S>
+__device__ __forceinline__ void stage16(float *sV, const S *src, int n, int d, int c0) {
+#pragma unroll 4
+  for (int e = threadIdx.x; e < n * kRowCols; e += blockDim.x) {
+    const int k = e / kRowCols, c = e - k * kRowCols;
+    sV[e] = (c0 + c < d) ? (float)ldcg(src + (size_t)k * d + c0 + c) : 0.0f;
+  }
+}
+
+// Upward pass, eliminated block j of level l: y_j = L_j^{-1} b_j into Yt.
+__device__ inline void largeA2_rows(const Args<float> &a, int l, long long j, float *smem) {
+  const int n = a.p.n, d = a.d, r = threadIdx.x;
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  const float *Li = a.Li + (size_t)orig * nn;
+  for (int c0 = 0; c0 < d; c0 += kRowCols) {
+    if (l == 0 && a.B64) stage16(smem, a.B64 + (size_t)orig * nd, n, d, c0);
+    else stage16(smem, ((l == 0 && a.Bt) ? a.Bt : a.Y) + (size_t)orig * nd, n, d, c0);
+    __syncthreads();
+    if (r < n) {
+      float acc[kRowCols] = {};
+      rowprod16<false>(acc, Li, n, r, 0, r + 1, smem);  // L^{-1} is lower triangular
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c0 + c < d) a.Yt[(size_t)orig * nd + (size_t)r * d + c0 + c] = acc[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Upward pass, separator s = 2k of level l: b_s -= W_R(s-1)^T y_{s-1} + W_L(s+1)^T y_{s+1}
+// (Algorithm 5), with (W^T y)[r] = sum_q Wt[r][q] y[q] over the stored W^T rows.
+__device__ inline void largeB_rows(const Args<float> &a, int l, long long k, float *smem) {
+  const int n = a.p.n, d = a.d, r = threadIdx.x;
+  const long long Nl = a.p.Nl[l], s = 2 * k;
+  const bool hasM = (s >= 2), hasP = (s + 1 < Nl);
+  const long long orig = s << l;
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  const float *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const float *ys = a.Yt ? a.Yt : a.Y;
+  float *sM = smem, *sP = smem + (size_t)n * kRowCols;
+  for (int c0 = 0; c0 < d; c0 += kRowCols) {
+    if (hasM) stage16(sM, ys + (size_t)((s - 1) << l) * nd, n, d, c0);
+    if (hasP) stage16(sP, ys + (size_t)((s + 1) << l) * nd, n, d, c0);
+    __syncthreads();
+    if (r < n) {
+      float acc[kRowCols] = {};
+      if (hasM) rowprod16<false>(acc, W + (size_t)(s - 1) * nn, n, r, 0, n, sM);
+      if (hasP) rowprod16<false>(acc, W + (size_t)s * nn, n, r, 0, n, sP);
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c0 + c < d) {
+          const size_t o = (size_t)orig * nd + (size_t)r * d + c0 + c;
+          float base;
+          if (l == 0 && a.B64) base = (float)ldcg(a.B64 + o);
+          else if (l == 0 && a.Bt) base = ldcg(a.Bt + o);
+          else base = ldcg(a.Y + o);
+          a.Y[o] = base - acc[c];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// Downward pass, eliminated block j of level l (Algorithms 6, 2):
+// t = y_j - W_L x_{j-1} - W_R x_{j+1} with (W x)[q] = sum_p Wt[p][q] x[p], then
+// x_j = L_j^{-T} t, i.e. x[r] = sum_{q >= r} L^{-1}[q][r] t[q].
+__device__ inline void largeC_rows(const Args<float> &a, int l, long long j, float *smem) {
+  const int n = a.p.n, d = a.d, r = threadIdx.x;
+  const long long Nl = a.p.Nl[l];
+  const bool hasR = (j + 1 < Nl);
+  const long long orig = j << l;
+  const size_t nn = (size_t)n * n, nd = (size_t)n * d;
+  const float *W = a.Wb + (size_t)a.p.off[l] * nn;
+  const float *Li = a.Li + (size_t)orig * nn;
+  const float *Yj = (a.Yt ? a.Yt : a.Y) + (size_t)orig * nd;
+  float *sXm = smem, *sXp = smem + (size_t)n * kRowCols, *sT = smem + (size_t)2 * n * kRowCols;
+  for (int c0 = 0; c0 < d; c0 += kRowCols) {
+    stage16(sXm, a.Y + (size_t)((j - 1) << l) * nd, n, d, c0);
+    if (hasR) stage16(sXp, a.Y + (size_t)((j + 1) << l) * nd, n, d, c0);
+    __syncthreads();
+    if (r < n) {
+      float acc[kRowCols] = {};
+      rowprod16<true>(acc, W + (size_t)(j - 1) * nn, n, r, 0, n, sXm);
+      if (hasR) rowprod16<true>(acc, W + (size_t)j * nn, n, r, 0, n, sXp);
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        sT[r * kRowCols + c] = (c0 + c < d) ? ldcg(Yj + (size_t)r * d + c0 + c) - acc[c] : 0.0f;
+    }
+    __syncthreads();
+    if (r < n) {
+      float x[kRowCols] = {};
+      rowprod16<true>(x, Li, n, r, r, n, sT);
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c0 + c < d) {
+          const size_t o = (size_t)orig * nd + (size_t)r * d + c0 + c;
+          a.Y[o] = x[c];
+          if (a.X64) a.X64[o] = a.x_accumulate ? a.X64[o] + (double)x[c] : (double)x[c];
+        }
+    }
+    __syncthreads();
+  }
+}
+
 // C: downward pass for eliminated position j of level l.
 template <typename T>
 __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
@@ -694,35 +761,6 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
       __syncthreads();
     }
   T *Yo = a.Y + (size_t)orig * nd;
-  if (a.Li) {
-    // x = L^{-T} t as row tiles of products with the stored inverse:
-    // x[r] = sum_{k >= r} L^{-1}[k][r] t[k]; t stays in shared memory, x goes
-    // straight to Y (and X64)
-    const T *Li = a.Li + (size_t)orig * nn;
-    for (int R = 0; R < ntiles(n); ++R) {
-      const int r0 = R * kTile;
-      for (int c0 = 0; c0 < d; c0 += kNarrow) {
-        T acc[4] = {};
-        const View<T, true> Tv{sV + (size_t)c0 * lv + r0, lv, 1, d - c0, n - r0};  // (c, k) -> t[r0 + k][c0 + c]
-        gemm_tn_narrow(acc, Li + (size_t)r0 * n, n, n, r0, Tv, 0, n - r0, sA, sB);
-        const int r = r0 + (threadIdx.x >> 2);
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int c = c0 + 4 * (threadIdx.x & 3) + jj;
-          if (r < n && c < d) {
-            const size_t o = (size_t)r * d + c;
-            Yo[o] = acc[jj];
-            if (a.X64) {
-              double *xo = a.X64 + (size_t)orig * nd + o;
-              *xo = a.x_accumulate ? *xo + (double)acc[jj] : (double)acc[jj];
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-    return;
-  }
   trsv_bwd_blocked(a.Ld + (size_t)orig * nn, n, sV, d, work);
 #pragma unroll 4
   for (int e = threadIdx.x; e < n * d; e += blockDim.x) {

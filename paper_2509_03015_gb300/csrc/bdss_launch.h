@@ -23,7 +23,7 @@ cudaError_t launch_phaseB(const Args<T> &a, int l, int factor, int grid, size_t 
 template <typename T> cudaError_t launch_top(const Args<T> &a, int factor, size_t smem, cudaStream_t s);
 template <typename T> cudaError_t launch_phaseC(const Args<T> &a, int l, int grid, size_t smem, cudaStream_t s);
 template <typename T>
-cudaError_t launch_logdet(long long N, int n, const T *Ld, const double *Ltop, double *partial, int grid,
+cudaError_t launch_logdet(long long N, int n, int Ltop_level, const T *Ld, const double *Ltop, double *partial, int grid,
                           cudaStream_t s);
 cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
                             const double *B, float *R32, DevStatus *st, int with_norm, int grid, cudaStream_t s);

@@ -172,6 +172,30 @@ class Solver:
         _lib.check(st, "bdss_chunk_backsolve")
         return X
 
+    def tune_nstar(self, A_diag, A_sub, B, candidates=(1, 2, 4, 8, 16, 32, 64), reps=5):
+        """Autotune the crossover N_* (Sec. 3.3 leaves it to be determined
+        dynamically) on these inputs: every candidate the handle accepts is
+        timed over `reps` factor + solve calls with CUDA events on the
+        handle's stream, and the fastest is kept.  Returns (best, {N_*: ms})."""
+        times = {}
+        X = torch.empty(B.shape, dtype=torch.float64, device="cuda")
+        for c in candidates:
+            try:
+                self.set_option("nstar", c)
+            except _lib.BDSSError:
+                continue
+            self.factor_solve(A_diag, A_sub, B, X)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            for _ in range(reps):
+                self.factor_solve(A_diag, A_sub, B, X)
+            e1.record(self.stream)
+            e1.synchronize()
+            times[c] = e0.elapsed_time(e1) / reps
+        best = min(times, key=times.get)
+        self.set_option("nstar", best)
+        return best, times
+
     def factor_shift(self):
         """Relative diagonal shift sigma of the stored factors (mixed
         precision; 0 unless the unshifted FP32 factorisation failed)."""
