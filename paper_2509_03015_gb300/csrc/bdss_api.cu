@@ -42,6 +42,7 @@ struct bdss_ctx {
   double *Ltop = nullptr;
   void *Li = nullptr;    // large mixed path: L^{-1} of the eliminated blocks (N n n, FP32)
   float *Yt = nullptr;   // large mixed path: y of the eliminated blocks in solve passes (N n d_max)
+  float *Ltinv = nullptr;  // large mixed path: float(L_top) and its inverse (2 n n)
   float *Y32 = nullptr;  // mixed: working RHS / correction (N n d_max)
   float *R32 = nullptr;  // mixed: FP32 residual (N n d_max)
   double *partial = nullptr;  // log-det partial sums
@@ -261,6 +262,7 @@ static Args<T> base_args(bdss_ctx *h) {
   a.tf32 = h->tf32;
   a.tmap_w = h->d_tmap;
   a.Li = (T *)h->Li;
+  a.Ltinv = (T *)h->Ltinv;
   return a;
 }
 
@@ -399,6 +401,7 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->emu.xmax);
   cudaFree(h->Li);
   cudaFree(h->Yt);
+  cudaFree(h->Ltinv);
   cudaFree(h->Y32);
   cudaFree(h->R32);
   cudaFree(h->partial);
@@ -485,6 +488,7 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
     if (h->large) {  // inverse factors and the y buffer of the solve passes
       ok = ok && ws_alloc(h, &h->Li, (size_t)N * nn * sizeof(float));
       ok = ok && ws_alloc(h, (void **)&h->Yt, nd * sizeof(float));
+      ok = ok && ws_alloc(h, (void **)&h->Ltinv, 2 * nn * sizeof(float));
     }
     if (ok && h->large && d_max <= kEmuDp) {  // the tensor-core FP64 residual
       ok = ws_alloc(h, (void **)&h->emu.Aslc, emu_aslc_bytes(N, n));

@@ -42,7 +42,7 @@ constexpr int kTraceSlots = 256;  // grid-barrier release stamps kept per launch
 
 struct DevStatus {
   unsigned int bar_count;  // arrivals at the current grid barrier
-  unsigned int bar_gen;    // generation of the grid barrier
+  unsigned int bar_gen;    // unused (the grid barrier counts arrivals only)
   int status;              // 0 = ok, else a bdss_status code
   int pad;
   long long level;         // NOT_SPD: level and original block of the pivot
@@ -89,6 +89,8 @@ struct Args {
   T *Li;                 // large FP32 path: L^{-1} of every eliminated block (slot of
                          // its original index, row-major n x n, zero above the
                          // diagonal), formed by the factorisation; null elsewhere
+  T *Ltinv;              // large FP32 path: float(L_top) then its inverse (2 n^2), for
+                         // the solve passes' top block; null elsewhere
   T *Yt;                 // large FP32 path, solve passes: y_j = L_j^{-1} b_j of the
                          // eliminated blocks (N x n x d), kept apart from Y because
                          // row tiles of one block are formed by several CTAs
@@ -166,6 +168,20 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
 // timeout_ns (or an iteration cap) the waiting CTA records BDSS_ERR_TIMEOUT
 // and returns false; any recorded error also makes it return false.  The
 // caller must return from the kernel when it gets false.
+//
+// The arrival counter only grows during a launch (the host clears it before
+// each launch): barrier `index` (the launch's barriers are numbered 0, 1, ...
+// in order) is released once (index + 1) x gridDim arrivals have been made.
+// Each CTA makes one acquire-release add (its CTA's writes, ordered before it
+// by the CTA barrier, are released with it) and then polls with acquire
+// loads, so no CTA resets or bumps a second word on the release path.  The
+// CTA whose arrival completes the count stamps the release time.
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 static __device__ __noinline__ bool grid_barrier(DevStatus *st, long long timeout_ns, int index, int skip) {
   __shared__ int s_ok;
   __syncthreads();
@@ -174,25 +190,20 @@ static __device__ __noinline__ bool grid_barrier(DevStatus *st, long long timeou
     if (ld_relaxed_i32(&st->status) != 0) {
       ok = 0;
     } else {
-      const unsigned gen = ld_acquire_u32(&st->bar_gen);
+      const unsigned target = (unsigned)(index + 1) * gridDim.x;
       const bool skip_me = (skip == index) && (blockIdx.x == 0);
-      bool released = false;
+      unsigned cur;
       if (!skip_me) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&st->bar_count, 1u);
-        if (prev == gridDim.x - 1) {
-          if (index >= 0 && index < kTraceSlots) st->trace[index] = global_ns();
-          atomicExch(&st->bar_count, 0u);
-          __threadfence();
-          atomicAdd(&st->bar_gen, 1u);
-          released = true;
-        }
+        cur = atom_add_acq_rel_u32(&st->bar_count, 1u) + 1u;
+        if (cur == target && index >= 0 && index < kTraceSlots) st->trace[index] = global_ns();
+      } else {
+        cur = ld_acquire_u32(&st->bar_count);
       }
-      if (!released) {
+      if (cur < target) {
         const long long t0 = global_ns();
         const unsigned long long cap = 1000000ull + (unsigned long long)(timeout_ns / 16);
         unsigned long long spins = 0;
-        while (ld_acquire_u32(&st->bar_gen) == gen) {
+        while (ld_acquire_u32(&st->bar_count) < target) {
           if (ld_relaxed_i32(&st->status) != 0) { ok = 0; break; }
           ++spins;
           if ((spins & 31) == 0 && (global_ns() - t0 > timeout_ns || spins > cap)) {
@@ -200,10 +211,9 @@ static __device__ __noinline__ bool grid_barrier(DevStatus *st, long long timeou
             ok = 0;
             break;
           }
-          __nanosleep(64);
+          if (spins > 64) __nanosleep(32);
         }
       }
-      __threadfence();
     }
     s_ok = ok;
   }

@@ -164,11 +164,12 @@ __host__ __device__ inline size_t smem_large(int n, int d, int esz) {
 // column + 1.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_flag) {
+__device__ __noinline__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_flag, T *Dinv = nullptr) {
   const int nt = ntiles(n);
   T *sT = smem;                              // 64 x 65 tile
   T *sA = sT + kTile * kTilePad;
   T *sB = sA + kKc * kTilePad;
+  T *sP2 = sB + kKc * kTilePad;              // panel rows when Dinv is given (64 x 65)
   const int ld = kTilePad;
   auto src = [&](int r, int c) -> T {      // element of the matrix before step 0
     if (src_sym) return T(0.5) * ((T)ldcg(src_sym + (long long)r * n + c) + (T)ldcg(src_sym + (long long)c * n + r));
@@ -192,8 +193,50 @@ __device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_
       const int r = e / kb, c = e - r * kb;
       if (c <= r) M[(long long)(k0 + r) * n + k0 + c] = sT[r * ld + c];
     }
+    if (Dinv) {
+      // L_kk^{-1} (the diagonal tile of L^{-1}): unit vectors through the tile
+      // substitution once, then every solve with this tile is a product
+      T *sI = sA;  // 64 x 65 (sA and sB are contiguous)
+      __syncthreads();
+      for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = e / kTile, c = e - r * kTile;
+        sI[r * ld + c] = (r == c && r < kb) ? T(1) : T(0);
+      }
+      __syncthreads();
+      trsv_tile_fwd(sT, ld, kb, sI, ld, kb);
+      for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+        const int r = e / kb, c = e - r * kb;  // (L_kk^{-1})[r][c] = entry r of solved vector c
+        Dinv[(long long)(k0 + r) * n + k0 + c] = (c <= r) ? sI[c * ld + r] : T(0);
+      }
+      __syncthreads();
+      // panel below: L_ik = S_ik L_kk^{-T}, i.e. L_ik[r][c] = sum_q S_ik[r][q] L_kk^{-1}[c][q]
+      const View<T> Dk{Dinv + (long long)k0 * n + k0, n, 1, kb, kb};
+      for (int i = k + 1; i < nt; ++i) {
+        const int i0 = i * kTile, ib = min(kTile, n - i0);
+#pragma unroll 4
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+          const int r = e / kTile, c = e - r * kTile;
+          T v = T(0);
+          if (r < ib && c < kb) v = first ? src(i0 + r, k0 + c) : ldcg(M + (long long)(i0 + r) * n + k0 + c);
+          sP2[r * ld + c] = v;
+        }
+        __syncthreads();
+        T acc[4][4] = {};
+        const View<T, true> Pr{sP2, ld, 1, ib, kb};
+        gemm_nt_tile(acc, Pr, 0, Dk, 0, kb, sA, sB);
+        const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) {
+            const int r = 4 * tm + a2, c = 4 * tn + b2;
+            if (r < ib && c < kb) M[(long long)(i0 + r) * n + k0 + c] = acc[a2][b2];
+          }
+        __syncthreads();
+      }
+    }
     // panel below: L_ik = S_ik L_kk^{-T}: each row x solves L_kk x = s
-    for (int i = k + 1; i < nt; ++i) {
+    for (int i = k + 1; i < nt && !Dinv; ++i) {
       const int i0 = i * kTile, ib = min(kTile, n - i0);
       // reuse the gemm staging area for the panel rows (ib x kb)
       T *sP = sA;  // needs kTile x kTilePad: sA and sB are contiguous 2 * kKc * kTilePad = kTile * kTilePad
@@ -241,7 +284,7 @@ __device__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_
 // n + 1), L (n x n, reciprocal diagonal) in global memory, blocked by 64-row
 // tiles: gemm update from the solved rows, then the triangular tile.
 template <typename T>
-__device__ void trsv_fwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
+__device__ void trsv_fwd_blocked(const T *L, int n, T *sV, int nv, T *smem, const T *Dinv = nullptr) {
   const int nt = ntiles(n), lv = n + 1;
   T *sT = smem;
   T *sA = sT + kTile * kTilePad;
@@ -265,6 +308,26 @@ __device__ void trsv_fwd_blocked(const T *L, int n, T *sV, int nv, T *smem) {
           }
         __syncthreads();
       }
+    }
+    if (Dinv) {
+      // the diagonal tile's solve as a product with its stored inverse:
+      // v[r0 + i] = sum_q L_RR^{-1}[i][q] v[r0 + q], 64 vectors at a time
+      const View<T> Dr{Dinv + (long long)r0 * n + r0, n, 1, rb, rb};
+      for (int c0 = 0; c0 < nv; c0 += kTile) {
+        T acc[4][4] = {};
+        const View<T, true> Vc{sV + (long long)c0 * lv + r0, lv, 1, nv - c0, rb};
+        gemm_nt_tile(acc, Dr, 0, Vc, 0, rb, sA, sB);
+        const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int i = 4 * tm + a, c = c0 + 4 * tn + b;
+            if (i < rb && c < nv) sV[(long long)c * lv + r0 + i] = acc[a][b];
+          }
+        __syncthreads();
+      }
+      continue;
     }
 #pragma unroll 4
     for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
@@ -324,7 +387,10 @@ __device__ bool largeA1(const Args<T> &a, int l, long long j, T *smem, int *s_fl
   const int n = a.p.n;
   const long long orig = j << l;
   T *M = a.Ld + orig * (long long)n * n;
-  const int bad = chol_blocked(M, n, l == 0 ? a.A_diag + orig * (long long)n * n : nullptr, smem, s_flag);
+  // FP32 with stored inverses: the diagonal tiles of L^{-1} are formed here,
+  // and every tile solve after them is a product
+  T *Dinv = a.Li ? a.Li + orig * (long long)n * n : nullptr;
+  const int bad = chol_blocked(M, n, l == 0 ? a.A_diag + orig * (long long)n * n : nullptr, smem, s_flag, Dinv);
   if (bad) {
     if (threadIdx.x == 0) set_status(a.st, kStNotSPD, l, orig);
     __syncthreads();
@@ -397,7 +463,7 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
     sV[(size_t)cc * lv + i] = val;
   }
   __syncthreads();
-  trsv_fwd_blocked(a.Ld + (size_t)orig * nn, n, sV, nv, work);
+  trsv_fwd_blocked(a.Ld + (size_t)orig * nn, n, sV, nv, work, factor && a.Li ? a.Li + (size_t)orig * nn : nullptr);
   // write back
   T *W = a.Wb + (size_t)a.p.off[l] * nn;
   for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
@@ -416,7 +482,9 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
       const int nu = u1 - u0;
       for (int e = threadIdx.x; e < n * nu; e += blockDim.x) {
         const int i = e / nu, u = u0 + e - i * nu;
-        Li[(size_t)i * n + u] = sV[(size_t)(u + nW - c0) * lv + i];
+        // the diagonal tiles were formed by the Cholesky task and are read
+        // by this level's other substitution tasks: left as they are
+        if (i / kTile != u / kTile) Li[(size_t)i * n + u] = sV[(size_t)(u + nW - c0) * lv + i];
       }
     }
   }
@@ -778,7 +846,7 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
 // Top block in FP64: Ltop <- D (from Ld slot 0, or sym(A_00) if no level),
 // blocked Cholesky in place, then x_0 = L^{-T} L^{-1} b_0.
 template <typename T>
-__device__ bool largeTop(const Args<T> &a, bool factor, double *smem, int *s_flag) {
+__device__ __noinline__ bool largeTop(const Args<T> &a, bool factor, double *smem, int *s_flag) {
   const int n = a.p.n, d = a.d, L = a.p.L, lv = n + 1;
   const size_t nn = (size_t)n * n;
   if (factor) {
@@ -792,6 +860,65 @@ __device__ bool largeTop(const Args<T> &a, bool factor, double *smem, int *s_fla
       if (threadIdx.x == 0) set_status(a.st, kStNotSPD, L, 0);
       __syncthreads();
       return false;
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (a.Ltinv) {
+        // the FP32 solve passes apply the top factor as products with L^{-1}:
+        // float(L) into Ltinv[0 .. n^2), then its inverse into Ltinv[n^2 ..),
+        // 64 unit vectors at a time through the blocked substitution
+        float *Lf = a.Ltinv, *Li = a.Ltinv + nn;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Lf[e] = (float)a.Ltop[e];
+        __syncthreads();
+        float *sV = reinterpret_cast<float *>(smem);
+        float *work = sV + (size_t)kTile * lv;
+        for (int u0 = 0; u0 < n; u0 += kTile) {
+          const int nu = min(kTile, n - u0);
+          for (int e = threadIdx.x; e < nu * n; e += blockDim.x) {
+            const int c = e / n, i = e - c * n;
+            sV[(size_t)c * lv + i] = (i == u0 + c) ? 1.0f : 0.0f;
+          }
+          __syncthreads();
+          trsv_fwd_blocked(Lf, n, sV, nu, work);
+          for (int e = threadIdx.x; e < n * nu; e += blockDim.x) {
+            const int i = e / nu, c = e - i * nu;
+            Li[(size_t)i * n + u0 + c] = sV[(size_t)c * lv + i];
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (d > 0 && a.Ltinv) {
+      // x_0 = L^{-T} (L^{-1} b_0), a thread per row, FP32 like the rest of the pass
+      const float *Li = a.Ltinv + nn;
+      float *sB = reinterpret_cast<float *>(smem), *sY = sB + (size_t)n * kRowCols;
+      const int r = threadIdx.x;
+      for (int c0 = 0; c0 < d; c0 += kRowCols) {
+        if (L == 0 && a.B64) stage16(sB, a.B64, n, d, c0);
+        else stage16(sB, (L == 0 && a.Bt) ? a.Bt : a.Y, n, d, c0);
+        __syncthreads();
+        if (r < n) {
+          float y[kRowCols] = {};
+          rowprod16<false>(y, Li, n, r, 0, r + 1, sB);
+#pragma unroll
+          for (int c = 0; c < kRowCols; ++c) sY[r * kRowCols + c] = y[c];
+        }
+        __syncthreads();
+        if (r < n) {
+          float x[kRowCols] = {};
+          rowprod16<true>(x, Li, n, r, r, n, sY);
+#pragma unroll
+          for (int c = 0; c < kRowCols; ++c)
+            if (c0 + c < d) {
+              const size_t o = (size_t)r * d + c0 + c;
+              a.Y[o] = x[c];
+              if (a.X64) a.X64[o] = a.x_accumulate ? a.X64[o] + (double)x[c] : (double)x[c];
+            }
+        }
+        __syncthreads();
+      }
+      return true;
     }
   }
   if (d > 0) {
