@@ -77,6 +77,11 @@ struct bdss_ctx {
   CUtensorMap emu_maps[2];
   int emu_ready = 0;     // buffers allocated and maps encoded
   int emu_on = 0;        // option: use them
+  // FP64 tiled path: Schur products on the tensor cores (digit slices of W)
+  unsigned short *Wslc = nullptr;  // (N - 1) x S x n x np BF16
+  int *Wexp = nullptr;             // (N - 1) x n row exponents
+  int schur_emu_ready = 0;
+  int schur_emu_on = 0;
   bool emu_sliced = false;
   int skip_barrier = 0;
   // stats of the last call
@@ -266,6 +271,32 @@ static Args<T> base_args(bdss_ctx *h) {
   return a;
 }
 
+// Separator update of level l on the tensor cores (FP64 factorisation):
+// slice the level's stored couplings, form D and the next level's E, then the
+// separators' RHS tiles (when the pass carries right-hand sides) on the ALU.
+static cudaError_t schur_emu_level(bdss_ctx *h, const Args<double> &b, int l) {
+  const Plan &p = h->plan;
+  const long long Nl = p.Nl[l];
+  const size_t nn = (size_t)p.n * p.n;
+  kt_begin(h, BDSS_KT_SLICE);
+  cudaError_t e = launch_emu_slice_w(Nl - 1, p.n, b.Wb + (size_t)p.off[l] * nn, h->Wslc, h->Wexp, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  if (e != cudaSuccess) return e;
+  kt_begin(h, BDSS_KT_SCHUR_TC);
+  e = launch_emu_schur(Nl, p.n, l, h->Wslc, h->Wexp, b.A_diag, b.Ld, b.Eb + (size_t)p.off[l + 1] * nn, h->dst,
+                       h->timeout_ns, h->sms, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  if (e != cudaSuccess || b.d == 0) return e;
+  kt_begin(h, h->kt_cls);
+  e = launch_large_sub<double>(b, l, kSubBRhsOnly, 1, grid_for(h, large_sub_tasks(p, l, kSubBRhsOnly, 1, b.d, 8, 0, 0)),
+                               h->smem, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  return e;
+}
+
 // One factor and/or RHS pass over all levels, persistent or per level.
 // Large-block path: three tile sub-phases per level (see bdss_large.cu).
 template <typename T>
@@ -277,12 +308,16 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   // Schur-update tiles use that kernel and the Cholesky / substitution tasks
   // keep the two-CTA FP32 kernel.
   const bool tc_factor = sizeof(T) == 4 && h->tf32 && factor;
+  // FP64 factorisation with the Schur products on the tensor cores: sub-phase
+  // by sub-phase as well (the slicing and the product kernels are launches
+  // of their own)
+  const bool emu_factor = sizeof(T) == 8 && factor && h->schur_emu_on;
   const int inv = a.Li ? 1 : 0;
   Args<T> b = a;
   if (!rhs) b.d = 0;
   // solve passes with the stored inverses keep y of the eliminated blocks in Yt
   b.Yt = (!factor && inv) ? (T *)h->Yt : nullptr;
-  if (h->persistent && !tc_factor) {
+  if (h->persistent && !tc_factor && !emu_factor) {
     long long most = 1;
     for (int l = 0; l < p.L; ++l)
       for (int sub = 0; sub < 4; ++sub) {
@@ -301,6 +336,12 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < p.L && e == cudaSuccess; ++l)
     for (int sub = factor ? 0 : 1; sub < 3 && e == cudaSuccess; ++sub) {
+      if constexpr (sizeof(T) == 8) {
+        if (emu_factor && sub == 2) {
+          e = schur_emu_level(h, b, l);
+          continue;
+        }
+      }
       kt_begin(h, (tc_factor && sub == 2) ? BDSS_KT_SCHUR_TC : h->kt_cls);
       e = launch_large_sub<T>(b, l, sub, f, grid_for(h, large_sub_tasks(p, l, sub, f, b.d, esz, h->tf32, inv)),
                               h->smem, h->stream);
@@ -399,6 +440,8 @@ bdss_status bdss_destroy(bdss_handle h) {
   cudaFree(h->emu.Xslc);
   cudaFree(h->emu.xexp);
   cudaFree(h->emu.xmax);
+  cudaFree(h->Wslc);
+  cudaFree(h->Wexp);
   cudaFree(h->Li);
   cudaFree(h->Yt);
   cudaFree(h->Ltinv);
@@ -509,6 +552,19 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
       }
     }
   }
+  if (ok && h->large && prec == BDSS_FP64 && N > 1) {  // Schur products on the tensor cores
+    ok = ws_alloc(h, (void **)&h->Wslc, emu_wslc_bytes(N - 1, n));
+    ok = ok && ws_alloc(h, (void **)&h->Wexp, (size_t)(N - 1) * n * sizeof(int));
+    if (ok) {
+      const cudaError_t ec = emu_configure();
+      if (ec != cudaSuccess) {
+        bdss_destroy(h);
+        return cuda_fail(ec);
+      }
+      h->schur_emu_ready = 1;
+      h->schur_emu_on = 1;
+    }
+  }
   if (!ok) {
     cudaGetLastError();  // clear the allocation error
     bdss_destroy(h);
@@ -567,6 +623,11 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
     case BDSS_OPT_SHIFT:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
       h->shift_on = (int)value;
+      return BDSS_OK;
+    case BDSS_OPT_SCHUR_EMU:
+      if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
+      if (value && !h->schur_emu_ready) return BDSS_ERR_UNSUPPORTED;
+      h->schur_emu_on = (int)value;
       return BDSS_OK;
     case BDSS_OPT_RESIDUAL_EMU:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;

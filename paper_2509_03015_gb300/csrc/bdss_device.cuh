@@ -320,6 +320,33 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return y;
 }
 
+// Pivot of the Cholesky sweeps: 1/sqrt(x) for a positive finite x with five
+// FP64 instructions on the critical path (each holds a warp's FP64 issue for
+// ~64 cycles on this GPU).  The seed is the FP32 reciprocal square root of x
+// cut to FP32 by integer operations (relative error below 2^-22 together);
+// one third-order step on f(y) = 1/y^2 - x,
+//   e = 1 - x y^2,   y <- y + y e (1/2 + 3/8 e),
+// leaves a truncation error of about (5/16) e^3 < 2^-64, so the result is
+// within an ulp or two.  Outside the FP32 exponent range: 1 / sqrt(x).
+__device__ __forceinline__ float rsqrt_pivot(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_pivot(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex < 1023 - 120 || ex > 1023 + 120) return 1.0 / sqrt(x);
+  const float xf = __int_as_float(((ex - 1023 + 127) << 23) | (int)((b >> 29) & 0x7FFFFF));
+  const int yb = __float_as_int(rsqrtf(xf));
+  const double y = __longlong_as_double(((long long)(((yb >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                        ((long long)(yb & 0x7FFFFF) << 29));
+  const double e = fma(-x, y * y, 1.0);
+  return fma(y, e * fma(e, 0.375, 0.5), y);
+}
+// x > 0 and finite, from the bits (no FP64 compare on the pivot path).
+__device__ __forceinline__ bool pivot_ok(float x) { return x > 0.0f && isfinite(x); }
+__device__ __forceinline__ bool pivot_ok(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && (int)(b >> 52) < 0x7FF;
+}
+
 // Cholesky of the staged lower triangle (Algorithm 1, potrf), in place,
 // right-looking: per column, warp 0 takes the pivot and scales the column,
 // then every thread updates the trailing lower triangle, so the FP64 work
@@ -371,7 +398,8 @@ constexpr TriTable make_tri_table() {
 }
 static __device__ const TriTable g_tri = make_tri_table();
 
-// Barrier among the update warps only (warps 1.., named barrier 1).
+// Barrier among the update warps only (every warp but the current pivot
+// warp, named barrier 1).
 __device__ __forceinline__ void update_warps_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x - 32) : "memory");
 }
@@ -380,7 +408,7 @@ __device__ __forceinline__ void update_warps_sync() {
 // (Algorithm 1's potrf and trsm in one right-looking sweep):
 //   L = chol(S) in place (diagonal <- 1 / L_kk), and for every staged vector
 //   w (rows of V1 and V2, stride ld): w <- L^{-1} w.
-// Warp 0 finishes the next column (its update and pivot) while the other
+// One warp finishes the next column (its update and pivot) while the other
 // warps apply the current column to the trailing triangle and to the
 // vectors, so one pivot latency per column is exposed instead of a pivot
 // plus a barrier-separated update and a separate substitution.  Each entry
@@ -395,8 +423,8 @@ __device__ int chol_fused(T *s, int ld, int n, T *V1, int nv1, T *V2, int nv2, i
   int bad = 0;
   if (tid < 32) {  // column 0
     const T dkk = s[0];
-    const bool ok = (dkk > T(0)) && isfinite(dkk);
-    const T r = rsqrt_nr(ok ? dkk : T(1));
+    const bool ok = pivot_ok(dkk);
+    const T r = rsqrt_pivot(ok ? dkk : T(1));
     for (int i = 1 + lane; i < n; i += 32) s[i * ld] *= r;
     if (lane == 0) {
       s[0] = r;
@@ -405,9 +433,14 @@ __device__ int chol_fused(T *s, int ld, int n, T *V1, int nv1, T *V2, int nv2, i
     }
   }
   if (__syncthreads_or(bad)) return 1;
-  const int ut = tid - 32, un = blockDim.x - 32;  // update-thread index / count
+  // The pivot warp of column k+1 cycles over warps 0..3, which sit on the
+  // SM's four sub-partitions: every CTA's pivot chain would otherwise share
+  // one sub-partition's FP64 unit with that CTA's update work.
+  const int warp = tid >> 5, nw = blockDim.x >> 5, pcyc = nw < 4 ? nw : 4;
+  const int un = blockDim.x - 32;  // update-thread count
   for (int k = 0; k + 1 < n; ++k) {
-    if (tid < 32) {
+    const int pw = (k + 1) % pcyc;
+    if (warp == pw) {
       // column k+1: apply column k, pivot, scale (rows k+1+lane, k+33+lane)
       const int i0 = k + 1 + lane, i1 = i0 + 32;
       const T lk = s[(k + 1) * ld + k];
@@ -415,8 +448,8 @@ __device__ int chol_fused(T *s, int ld, int n, T *V1, int nv1, T *V2, int nv2, i
       if (i0 < n) v0 = fma(-s[i0 * ld + k], lk, s[i0 * ld + k + 1]);
       if (i1 < n) v1 = fma(-s[i1 * ld + k], lk, s[i1 * ld + k + 1]);
       const T dkk = __shfl_sync(0xffffffffu, v0, 0);
-      const bool ok = (dkk > T(0)) && isfinite(dkk);
-      const T r = rsqrt_nr(ok ? dkk : T(1));
+      const bool ok = pivot_ok(dkk);
+      const T r = rsqrt_pivot(ok ? dkk : T(1));
       if (i0 < n) s[i0 * ld + k + 1] = lane == 0 ? r : v0 * r;
       if (i1 < n) s[i1 * ld + k + 1] = v1 * r;
       if (lane == 0 && !ok) {
@@ -426,6 +459,7 @@ __device__ int chol_fused(T *s, int ld, int n, T *V1, int nv1, T *V2, int nv2, i
     } else {
       // vectors: w[k] <- w[k] / L_kk, then w[j] -= w[k] L[j][k] for j > k;
       // trailing triangle j >= k+2: S[i][j] -= L[i][k] L[j][k]
+      const int ut = warp < pw ? tid : tid - 32;  // index among the update threads
       const T rk = s[k * ld + k];
       for (int v = ut; v < nv; v += un) {
         T *w = v < nv1 ? V1 + v * ld : V2 + (v - nv1) * ld;

@@ -524,8 +524,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-cudaError_t encode_bf16_2d(CUtensorMap *out, void *base, unsigned long long cols, unsigned long long rows,
-                           unsigned box_cols, unsigned box_rows) {
+cudaError_t encode_fn(EncodeTiledFn *out) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -535,6 +534,15 @@ cudaError_t encode_bf16_2d(CUtensorMap *out, void *base, unsigned long long cols
     if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
     fn = (EncodeTiledFn)p;
   }
+  *out = fn;
+  return cudaSuccess;
+}
+
+cudaError_t encode_bf16_2d(CUtensorMap *out, void *base, unsigned long long cols, unsigned long long rows,
+                           unsigned box_cols, unsigned box_rows) {
+  EncodeTiledFn fn = nullptr;
+  const cudaError_t e = encode_fn(&fn);
+  if (e != cudaSuccess) return e;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
   const cuuint32_t box[2] = {box_cols, box_rows};
@@ -544,6 +552,377 @@ cudaError_t encode_bf16_2d(CUtensorMap *out, void *base, unsigned long long cols
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+// ===========================================================================
+// FP64-accurate Schur products of the tiled FP64 factorisation on the tensor
+// cores (the separator update of Algorithm 3, 64 < n <= 256).
+//
+// At level l the stored coupling blocks M_b (b = 0 .. N_l - 2; row m of M_b is
+// column m of the coupling solve W, so D -= M M^T) are cut row by row in the
+// same fixed-point digits as the operator rows of the residual: exponent
+// E_b[m] with max_k |M_b[m][k]| < 2^E and ten planes
+// Wslc[((b S + p) n + m) np + k], zero for k >= n.  Separator s = 2k needs
+//   D_s     = D - M_{s-1} M_{s-1}^T - M_s M_s^T   (lower triangle),
+//   E_{l+1} = - M_{s+1} M_s^T                     (slot k of level l + 1),
+// computed over 128 x 16 output tiles.  Each product M_a M_b^T of a tile is
+// one accumulation round: per K chunk of 64 the B operand is the ten slices
+// of rows c0 .. c0 + 15 of M_b (one 3-D TMA box, N = 160 rows) and the A
+// operand slice p of rows m0 .. m0 + 127 of M_a, written at TMEM column 16 p,
+// so slice pair (p, q) lands on the accumulator of diagonal p + q as in the
+// residual.  With K <= 256, |ACC_t| <= 10 x 256 x 32 x 32 < 2^22: every sum is
+// exact.  The epilogue scales a round by 2^(E_a[r] + E_b[c] - 118) and adds
+// the rounds of a tile in FP64; the only error is the 59-bit cut of the
+// inputs, below an FP64 product's rounding in the normwise sense.
+// ===========================================================================
+constexpr int kSchurN = 16;      // output columns of a tile
+constexpr int kSchurRounds = 2;  // products of one tile at most
+
+// One warp per row b n + m of the level's stored blocks.
+__global__ void __launch_bounds__(256) k_emu_slice_w(long long rows, int n, int np, const double *W,
+                                                     unsigned short *Wslc, int *Wexp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long row = (long long)blockIdx.x * 8 + warp;
+  if (row >= rows) return;
+  const long long b = row / n;
+  const int m = (int)(row - b * n);
+  const double *src = W + (size_t)row * n;
+  double v[2][4];
+  unsigned long long mx = 0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = 4 * (lane + 32 * i) + t;
+      v[i][t] = k < n ? __ldg(src + k) : 0.0;
+      // |v| as bits: ordered like the values, a NaN above every finite value
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(v[i][t]));
+      mx = bits > mx ? bits : mx;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  const int E = emu_exp(mx);
+  if (lane == 0) Wexp[row] = E;
+  unsigned short *dst = Wslc + ((size_t)b * kS * n + m) * np;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int k = 4 * (lane + 32 * i);
+    if (k < np) emu_store_quad(v[i], E, dst + k, (size_t)n * np);
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct EmuSchurArgs {
+  long long Nl;          // positions of level l
+  int n, np, l;
+  const int *Wexp;       // (N_l - 1) x n row exponents of the level's stored blocks
+  const double *A_diag;  // level 0: the separators' D (symmetrised)
+  double *Ld;            // D blocks (slot s << l)
+  double *En;            // E blocks of level l + 1 (slot k)
+  DevStatus *st;
+  long long timeout_ns;
+};
+
+// Column tiles of row tile mt inside D's lower part (c0 < (mt + 1) 128).
+__host__ __device__ inline int schur_d_cols(int n, int mt) {
+  const int CT = (n + kSchurN - 1) / kSchurN, lim = (mt + 1) * kM / kSchurN;
+  return CT < lim ? CT : lim;
+}
+__host__ __device__ inline int schur_tiles_per_sep(int n) {
+  const int MT = (n + kM - 1) / kM, CT = (n + kSchurN - 1) / kSchurN;
+  int t = MT * CT;
+  for (int mt = 0; mt < MT; ++mt) t += schur_d_cols(n, mt);
+  return t;
+}
+
+// Output tile u of the level: separator k, a D tile (lower set) or an E tile,
+// and its rounds (stored blocks of the A and B operands).
+struct SchurTile {
+  long long k, ra[kSchurRounds], rb[kSchurRounds];
+  int isD, mt, ct, nr;
+  // operands of round r (selects, so that the tile stays in registers)
+  __device__ long long a_of(int r) const { return r == 0 ? ra[0] : ra[1]; }
+  __device__ long long b_of(int r) const { return r == 0 ? rb[0] : rb[1]; }
+};
+__device__ __forceinline__ SchurTile schur_tile(long long u, long long Nl, int n) {
+  SchurTile T;
+  const int per = schur_tiles_per_sep(n);
+  const int MT = (n + kM - 1) / kM, CT = (n + kSchurN - 1) / kSchurN;
+  T.k = u / per;
+  int r = (int)(u - T.k * per);
+  const long long s = 2 * T.k;
+  T.isD = 0;
+  T.mt = 0;
+  T.ct = 0;
+  T.nr = 0;
+  for (int mt = 0; mt < MT; ++mt) {
+    const int c = schur_d_cols(n, mt);
+    if (r < c) {
+      T.isD = 1;
+      T.mt = mt;
+      T.ct = r;
+      break;
+    }
+    r -= c;
+  }
+  if (T.isD) {
+    if (s >= 2) {
+      T.ra[T.nr] = s - 1;
+      T.rb[T.nr] = s - 1;
+      ++T.nr;
+    }
+    if (s + 1 < Nl) {
+      T.ra[T.nr] = s;
+      T.rb[T.nr] = s;
+      ++T.nr;
+    }
+  } else {
+    T.mt = r / CT;
+    T.ct = r - T.mt * CT;
+    if (s + 2 < Nl) {
+      T.ra[0] = s + 1;
+      T.rb[0] = s;
+      T.nr = 1;
+    }
+  }
+  return T;
+}
+
+// Roles as in the residual kernel: warp 0 TMA, warp 1 MMA, warps 2-5 the
+// epilogue of one TMEM lane quarter each.  Every wait is bounded.
+__global__ void __launch_bounds__(kEmuThreads, 1)
+    k_emu_schur(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const __grid_constant__ EmuSchurArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t a_full[kAStages], a_empty[kAStages], b_full[kXStages], b_empty[kXStages];
+  __shared__ uint64_t acc_full, acc_empty, drain;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~(uintptr_t)1023);
+  unsigned char *Ast = base;                              // kAStages x 16 KB
+  unsigned char *Bst = base + (size_t)kAStages * kATile;  // kXStages x 20 KB
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.n, kchunks = a.np / kEmuKc;
+  const long long tiles = ((a.Nl + 1) / 2) * schur_tiles_per_sep(n);
+  volatile int *abort = &s_abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kAStages; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < kXStages; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 128);
+    mbar_init(&drain, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(&s_tmem, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  auto fail = [&]() {
+    *abort = 1;
+    set_status(a.st, kStTimeout, -1, -1);
+  };
+
+  if (warp == 0) {
+    // ---- TMA producer -------------------------------------------------------
+    if (lane == 0) {
+      int as = 0, bs = 0;
+      uint32_t aph = 0, bph = 0;
+      for (long long u = blockIdx.x; u < tiles && !*abort; u += gridDim.x) {
+        const SchurTile T = schur_tile(u, a.Nl, n);
+        for (int r = 0; r < T.nr && !*abort; ++r)
+          for (int kk = 0; kk < kchunks; ++kk) {
+            if (!emu_wait(&b_empty[bs], bph ^ 1, a.timeout_ns, abort)) { fail(); break; }
+            mbar_expect_tx(&b_full[bs], kXTile);
+            tma_load_3d(Bst + (size_t)bs * kXTile, &mapB, kk * kEmuKc, T.ct * kSchurN, (int)(T.b_of(r) * kS),
+                        &b_full[bs]);
+            if (++bs == kXStages) { bs = 0; bph ^= 1; }
+            for (int p = 0; p < kS; ++p) {
+              if (!emu_wait(&a_empty[as], aph ^ 1, a.timeout_ns, abort)) { fail(); break; }
+              mbar_expect_tx(&a_full[as], kATile);
+              tma_load_2d(Ast + (size_t)as * kATile, &mapA, kk * kEmuKc, (int)((T.a_of(r) * kS + p) * n + T.mt * kM),
+                          &a_full[as]);
+              if (++as == kAStages) { as = 0; aph ^= 1; }
+            }
+            if (*abort) break;
+          }
+      }
+      for (int s = 0; s < kAStages; ++s) {
+        const uint32_t ph = (s < as) ? aph : (aph ^ 1);
+        emu_wait(&a_full[s], ph, a.timeout_ns, nullptr);
+      }
+      for (int s = 0; s < kXStages; ++s) {
+        const uint32_t ph = (s < bs) ? bph : (bph ^ 1);
+        emu_wait(&b_full[s], ph, a.timeout_ns, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ------------------------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = emu_idesc(kM, kN);
+      int as = 0, bs = 0;
+      uint32_t aph = 0, bph = 0, eph = 0;
+      for (long long u = blockIdx.x; u < tiles && !*abort; u += gridDim.x) {
+        const SchurTile T = schur_tile(u, a.Nl, n);
+        for (int r = 0; r < T.nr && !*abort; ++r) {
+          if (!emu_wait(&acc_empty, eph, a.timeout_ns, abort)) { fail(); break; }
+          eph ^= 1;
+          tc_fence_after();
+          for (int kk = 0; kk < kchunks; ++kk) {
+            if (!emu_wait(&b_full[bs], bph, a.timeout_ns, abort)) { fail(); break; }
+            const unsigned char *bb = Bst + (size_t)bs * kXTile;
+            for (int p = 0; p < kS; ++p) {
+              if (!emu_wait(&a_full[as], aph, a.timeout_ns, abort)) { fail(); break; }
+              tc_fence_after();
+              const unsigned char *ab = Ast + (size_t)as * kATile;
+#pragma unroll
+              for (int ks = 0; ks < kEmuKc / 16; ++ks)
+                emu_mma_bf16(tmem + (uint32_t)(p * kSchurN), tc_desc_sw128(ab, ks * 32), tc_desc_sw128(bb, ks * 32),
+                             idesc);
+              tc_commit(&a_empty[as]);
+              if (++as == kAStages) { as = 0; aph ^= 1; }
+            }
+            tc_commit(&b_empty[bs]);
+            if (++bs == kXStages) { bs = 0; bph ^= 1; }
+            if (*abort) break;
+          }
+          tc_commit(&acc_full);
+        }
+      }
+      tc_commit(&drain);
+      emu_wait(&drain, 0, a.timeout_ns, nullptr);
+    }
+  } else {
+    // ---- epilogue: warps 2..5, TMEM lane quarter warp % 4 ---------------------
+    const int quarter = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    auto clear = [&]() {
+      for (int t = 0; t < kDiag; ++t) tmem_zero16(lane_base + (uint32_t)(t * kSchurN));
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      emu_arrive(&acc_empty);
+    };
+    clear();
+    uint32_t fph = 0;
+    const size_t nn = (size_t)n * n;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < tiles && !stop; u += gridDim.x) {
+      const SchurTile T = schur_tile(u, a.Nl, n);
+      if (T.nr == 0) continue;
+      const int row = T.mt * kM + 32 * quarter + lane;
+      double acc[kSchurN];
+#pragma unroll
+      for (int c = 0; c < kSchurN; ++c) acc[c] = 0.0;
+      for (int r = 0; r < T.nr; ++r) {
+        int ok = 0;
+        if (lane == 0) ok = emu_wait(&acc_full, fph, a.timeout_ns, abort) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) fail();
+          stop = true;
+          break;
+        }
+        if (lane != 0) emu_try(&acc_full, fph);
+        fph ^= 1;
+        tc_fence_after();
+        double v[kSchurN];
+        {
+          long long G[kSchurN];
+#pragma unroll
+          for (int c = 0; c < kSchurN; ++c) G[c] = 0;
+          for (int t = 0; t < kDiag; ++t) {
+            uint32_t rr[16];
+            tmem_ld16(lane_base + (uint32_t)(t * kSchurN), rr);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < kSchurN; ++c) G[c] = G[c] * 64 + (long long)__float2int_rn(__uint_as_float(rr[c]));
+            if (t == 6 || t == 13 || t == kDiag - 1) {
+              const double w = t == 6 ? 4722366482869645213696.0 /* 2^72 */ : t == 13 ? 1073741824.0 /* 2^30 */ : 1.0;
+#pragma unroll
+              for (int c = 0; c < kSchurN; ++c) {
+                v[c] = (t == 6) ? (double)G[c] * w : fma((double)G[c], w, v[c]);
+                G[c] = 0;
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        clear();
+        const int Ea = row < n ? __ldg(a.Wexp + (size_t)T.a_of(r) * n + row) : 0;
+#pragma unroll
+        for (int c = 0; c < kSchurN; ++c) {
+          const int col = T.ct * kSchurN + c;
+          const int Eb = col < n ? __ldg(a.Wexp + (size_t)T.b_of(r) * n + col) : 0;
+          // an Inf or NaN in either row (exponent field all ones: E = 1025)
+          // poisons the entry, as an FP64 product would
+          acc[c] += (Ea > 1024 || Eb > 1024) ? __longlong_as_double(0x7FF8000000000000LL)
+                                             : scalbn(v[c], Ea + Eb - 2 * kFrac);
+        }
+      }
+      if (stop || row >= n) continue;
+      const long long s = 2 * T.k;
+      if (T.isD) {
+        const long long orig = s << a.l;
+        double *Dg = a.Ld + (size_t)orig * nn + (size_t)row * n;
+        const double *Ag = a.A_diag + (size_t)orig * nn;
+#pragma unroll
+        for (int c = 0; c < kSchurN; ++c) {
+          const int col = T.ct * kSchurN + c;
+          if (col < n && col <= row) {
+            const double b0 = a.l == 0 ? 0.5 * (__ldg(Ag + (size_t)row * n + col) + __ldg(Ag + (size_t)col * n + row))
+                                       : Dg[col];
+            Dg[col] = b0 - acc[c];
+          }
+        }
+      } else {
+        double *Eg = a.En + (size_t)T.k * nn + (size_t)row * n;
+#pragma unroll
+        for (int c = 0; c < kSchurN; ++c) {
+          const int col = T.ct * kSchurN + c;
+          if (col < n) Eg[col] = -acc[c];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+cudaError_t encode_bf16_3d(CUtensorMap *out, void *base, unsigned long long cols, unsigned long long rows,
+                           unsigned long long planes, unsigned box_cols, unsigned box_rows, unsigned box_planes) {
+  EncodeTiledFn fn = nullptr;
+  const cudaError_t e = encode_fn(&fn);
+  if (e != cudaSuccess) return e;
+  const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)cols * rows * 2};
+  const cuuint32_t box[3] = {box_cols, box_rows, box_planes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 
 }  // namespace
 
@@ -564,7 +943,7 @@ cudaError_t emu_configure() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const void *kernels[] = {(const void *)k_emu_residual, (const void *)k_emu_slice_operator,
-                           (const void *)k_emu_slice_x};
+                           (const void *)k_emu_slice_x, (const void *)k_emu_schur};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -612,6 +991,47 @@ cudaError_t launch_emu_residual(long long N, int n, int d, const double *X, cons
   const long long tiles = N * ((n + kM - 1) / kM);
   const int grid = (int)(tiles < sms ? tiles : sms);
   k_emu_residual<<<grid, kEmuThreads, kResidualSmem, s>>>(b.maps[0], b.maps[1], k);
+  return cudaGetLastError();
+}
+
+size_t emu_wslc_bytes(long long nW, int n) { return (size_t)nW * kS * n * emu_np(n) * 2; }
+
+cudaError_t launch_emu_slice_w(long long nW, int n, const double *W, unsigned short *Wslc, int *Wexp,
+                               cudaStream_t s) {
+  if (n > 256) return cudaErrorInvalidValue;
+  const long long rows = nW * n;
+  if (rows <= 0) return cudaSuccess;
+  k_emu_slice_w<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(rows, n, emu_np(n), W, Wslc, Wexp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emu_schur(long long Nl, int n, int l, const unsigned short *Wslc, const int *Wexp,
+                             const double *A_diag, double *Ld, double *En, DevStatus *st, long long timeout_ns,
+                             int sms, cudaStream_t s) {
+  if (Nl < 2 || n > 256) return cudaErrorInvalidValue;
+  const int np = emu_np(n);
+  const long long nW = Nl - 1;
+  CUtensorMap mapA, mapB;
+  cudaError_t e = encode_bf16_2d(&mapA, (void *)Wslc, (unsigned long long)np, (unsigned long long)(nW * kS * n),
+                                 kEmuKc, kM);
+  if (e == cudaSuccess)
+    e = encode_bf16_3d(&mapB, (void *)Wslc, (unsigned long long)np, (unsigned long long)n,
+                       (unsigned long long)(nW * kS), kEmuKc, kSchurN, kS);
+  if (e != cudaSuccess) return e;
+  EmuSchurArgs k;
+  k.Nl = Nl;
+  k.n = n;
+  k.np = np;
+  k.l = l;
+  k.Wexp = Wexp;
+  k.A_diag = A_diag;
+  k.Ld = Ld;
+  k.En = En;
+  k.st = st;
+  k.timeout_ns = timeout_ns;
+  const long long tiles = ((Nl + 1) / 2) * schur_tiles_per_sep(n);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  k_emu_schur<<<grid, kEmuThreads, kResidualSmem, s>>>(mapA, mapB, k);
   return cudaGetLastError();
 }
 

@@ -45,4 +45,15 @@ cudaError_t launch_emu_residual(long long N, int n, int d, const double *X, cons
                                 double *R64, const EmuBuffers &b, DevStatus *st, long long timeout_ns, int sms,
                                 cudaStream_t s);
 
+// Schur products of the tiled FP64 factorisation on the tensor cores (see
+// bdss_emu.cu): the level's N_l - 1 stored coupling blocks W (n x n each) are
+// sliced into Wslc / Wexp, then the separators' D (lower, in Ld at slot s << l;
+// level 0 reads sym(A_diag)) and the next level's E (En, slot k) are formed.
+size_t emu_wslc_bytes(long long nW, int n);
+cudaError_t launch_emu_slice_w(long long nW, int n, const double *W, unsigned short *Wslc, int *Wexp,
+                               cudaStream_t s);
+cudaError_t launch_emu_schur(long long Nl, int n, int l, const unsigned short *Wslc, const int *Wexp,
+                             const double *A_diag, double *Ld, double *En, DevStatus *st, long long timeout_ns,
+                             int sms, cudaStream_t s);
+
 }  // namespace bdss

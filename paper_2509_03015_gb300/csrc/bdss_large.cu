@@ -57,6 +57,9 @@ __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem
     }
     const int nTB = largeB_tiles(n, factor, d);
     for (long long t = rank; t < nS * nTB; t += gridDim.x) largeB(a, l, t / nTB, (int)(t % nTB), factor, smem);
+  } else if (sub == kSubBRhsOnly) {
+    const int nR = largeB_tiles(n, false, d);
+    for (long long t = rank; t < nS * nR; t += gridDim.x) largeB(a, l, t / nR, (int)(t % nR), false, smem);
   } else {
     if constexpr (sizeof(T) == 4) {
       if (a.Li) {  // with the stored inverses, a thread per row
@@ -308,6 +311,7 @@ cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStre
 
 long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32, int inv) {
   const long long Nl = p.Nl[l], nE = Nl / 2, nS = (Nl + 1) / 2;
+  if (sub == kSubBRhsOnly) return nS * largeB_tiles(p.n, false, d);
   if (sub == kSubA1 || sub == kSubC) return nE;
   if (sub == kSubA2) {
     if (!factor && inv) return nE;

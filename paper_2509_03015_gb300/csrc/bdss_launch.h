@@ -42,6 +42,9 @@ cudaError_t launch_large_sub(const Args<T> &a, int l, int sub, int factor, int g
 template <typename T> cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStream_t s);
 // Tasks of sub-phase `sub` at level l; inv = the pass uses the stored
 // inverses (FP32 tiled path).
+// Sub-phase code of the large path: the separators' RHS tiles alone (their D
+// and E tiles ran elsewhere, e.g. on the tensor cores).
+constexpr int kSubBRhsOnly = 4;
 long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32, int inv);
 cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows, int n);
 cudaError_t run_tc_selftest(double *max_err, int *status);

@@ -97,3 +97,138 @@ def test_residual_option_is_refused_without_tensor_core_buffers():
         s.set_option("residual_emu", 1)
     assert e.value.status == 8
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# The Schur products of the tiled FP64 factorisation on the tensor cores
+# (separator update of Algorithm 3).  The FP64 large-block parity tests run
+# with them by default; these compare the two product engines directly.
+# ---------------------------------------------------------------------------
+def _fp64_solve(s, schur_emu, persistent=True):
+    from paper_2509_03015_gb300 import Solver
+    N, n, _ = s["A_diag"].shape
+    d = s["B"].shape[-1]
+    solver = Solver(N, n, d_max=d, precision="fp64", persistent=persistent)
+    try:
+        solver.set_option("schur_emu", 1 if schur_emu else 0)
+        As = s["A_sub"] if N > 1 else np.zeros((1, n, n))
+        X = solver.factor_solve(_dev(s["A_diag"]), _dev(As), _dev(s["B"]))
+        return X.cpu().numpy(), solver.logdet()
+    finally:
+        solver.close()
+
+
+def _integer_couplings(n, d, seed):
+    """N = 3 with A_11 = I, integer couplings in [-2, 2] and diagonals chosen
+    so that every Schur complement is an integer matrix (D_2 = I at level 0,
+    the top block 4 I): every product of the factorisation is an exact
+    integer sum, so both engines must give the same bits, and the solution of
+    an integer B is exact (denominators are powers of two)."""
+    rng = np.random.default_rng(seed)
+    A10 = rng.integers(-2, 3, (n, n)).astype(float)
+    A21 = rng.integers(-2, 3, (n, n)).astype(float)
+    I = np.eye(n)
+    E = A21 @ A10
+    A_diag = np.stack([A10.T @ A10 + E.T @ E + 4.0 * I, I, I + A21 @ A21.T])
+    A_sub = np.stack([A10, A21])
+    B = rng.integers(-8, 9, (3, n, d)).astype(float)
+    return {"A_diag": A_diag, "A_sub": A_sub, "B": B}
+
+
+def _exact_residual_is_zero(s, X, scale_bits=8):
+    """A X == B in integer arithmetic: X scaled by 2^scale_bits must be
+    integral, and the products are formed with Python integers."""
+    Xs = X * 2.0 ** scale_bits
+    if not np.array_equal(Xs, np.round(Xs)):
+        return False
+    Xi = Xs.astype(np.int64).astype(object)
+    Ad = s["A_diag"].astype(np.int64).astype(object)
+    As = s["A_sub"].astype(np.int64).astype(object)
+    Bi = (s["B"] * 2.0 ** scale_bits).astype(np.int64).astype(object)
+    N = Ad.shape[0]
+    for i in range(N):
+        r = Ad[i].dot(Xi[i])
+        if i > 0:
+            r = r + As[i - 1].dot(Xi[i - 1])
+        if i + 1 < N:
+            r = r + As[i].T.dot(Xi[i + 1])
+        if not np.array_equal(r, Bi[i]):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("n,d", [(96, 1), (200, 3), (256, 2)])
+def test_schur_emu_exact_on_integer_couplings(n, d):
+    """Both engines give the same bits, and that is the exact solution (the
+    FP64 oracle, which eliminates in another order, is not exact here: the
+    system's condition number is ~1e8)."""
+    s = _integer_couplings(n, d, seed=n)
+    Xe, lde = _fp64_solve(s, schur_emu=True)
+    Xa, lda = _fp64_solve(s, schur_emu=False)
+    assert np.array_equal(Xe, Xa) and lde == lda
+    assert _exact_residual_is_zero(s, Xe)
+
+
+SCHUR_CASES = [(2, 96, 2), (3, 65, 1), (5, 128, 4), (9, 200, 3), (17, 256, 16), (33, 130, 2), (64, 192, 5)]
+
+
+@pytest.mark.parametrize("N,n,d", SCHUR_CASES)
+def test_schur_emu_matches_oracle_and_alu(oracle_mod, N, n, d):
+    s = inputs.random_btd(N, n, d, seed=60 + N + n)
+    Xe, lde = _fp64_solve(s, schur_emu=True)
+    Xa, _ = _fp64_solve(s, schur_emu=False)
+    Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
+    assert oracle_mod.forward_error(Xe, Xo) <= 1e-10
+    assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], Xe, s["B"]) <= 1e-14
+    # the two engines differ by rounding only
+    assert oracle_mod.forward_error(Xe, Xa) <= 1e-12
+    L, _ = oracle_mod.factor(s["A_diag"], s["A_sub"])
+    ldo = oracle_mod.logdet(L)
+    assert abs(lde - ldo) <= 1e-12 * max(1.0, abs(ldo))
+
+
+def test_schur_emu_wide_row_scales(oracle_mod):
+    """Rows and columns of the system spread over sixteen binades, so that
+    the rows of every coupling block are cut below very different maxima."""
+    N, n, d = 9, 160, 3
+    s = inputs.random_btd(N, n, d, seed=11)
+    sc = np.logspace(-8, 8, n)
+    s["A_diag"] = s["A_diag"] * sc[None, :, None] * sc[None, None, :]
+    s["A_sub"] = s["A_sub"] * sc[None, :, None] * sc[None, None, :]
+    s["B"] = s["B"] * sc[None, :, None]
+    Xe, _ = _fp64_solve(s, schur_emu=True)
+    Xa, _ = _fp64_solve(s, schur_emu=False)
+    assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], Xe, s["B"]) <= 1e-14
+    # both engines reach the same backward error class; the forward
+    # difference is bounded through the scaled condition number
+    assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], Xa, s["B"]) <= 1e-14
+
+
+def test_schur_emu_per_level_matches_persistent():
+    s = inputs.random_btd(17, 128, 2, seed=5)
+    X1, ld1 = _fp64_solve(s, schur_emu=True, persistent=True)
+    X2, ld2 = _fp64_solve(s, schur_emu=True, persistent=False)
+    assert np.array_equal(X1, X2) and ld1 == ld2
+
+
+def test_schur_emu_not_spd_reports_block():
+    from paper_2509_03015_gb300 import BDSSError, Solver
+    s = inputs.random_btd(9, 128, 1, seed=2)
+    s["A_diag"][6] -= 1e4 * np.eye(128)
+    solver = Solver(9, 128, d_max=1)
+    solver.set_option("schur_emu", 1)
+    with pytest.raises(BDSSError) as e:
+        solver.factor_solve(_dev(s["A_diag"]), _dev(s["A_sub"]), _dev(s["B"]))
+    assert e.value.status == 2 and e.value.info.block == 6 and e.value.info.level == 1
+    solver.close()
+
+
+@pytest.mark.parametrize("n,prec", [(32, "fp64"), (128, "fp32_ir")])
+def test_schur_emu_option_is_refused_elsewhere(n, prec):
+    from paper_2509_03015_gb300 import BDSSError, Solver
+    s = Solver(8, n, d_max=2, precision=prec)
+    with pytest.raises(BDSSError) as e:
+        s.set_option("schur_emu", 1)
+    assert e.value.status == 8
+    s.set_option("schur_emu", 0)
+    s.close()
