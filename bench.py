@@ -133,6 +133,13 @@ def kernel_rooflines(kt, steps, units, N, n, d, mode, sms, mhz, emu=False):
         elif cls == "residual":
             work, unit, bound = 6.0 * n * n * d * N, "TFLOP/s", "alu"
             peak, pdef = fp64_peak(sms, mhz), "FP64 ALU (SMs x 2 DFMA/clk x 2 x clock)"
+        elif cls == "slice" and mode == "fp64":
+            work, unit, bound = accounting.emu_wslice_bytes(N, n), "GB/s", "hbm"
+            peak, pdef = pk["hbm_gbs"] * 1e9, f"HBM copy bandwidth ({pk['source']}); coupling blocks sliced"
+        elif cls == "schur_tc" and mode == "fp64":
+            work, unit, bound = accounting.emu_schur_mma_flops(N, n), "TFLOP/s", "tensor"
+            peak = pk["bf16_tflops"] * 1e12
+            pdef = f"BF16 dense ({pk['source']}); digit-slice products executed"
         elif cls == "slice":
             np_ = -(-n // 64) * 64
             work, unit, bound = 16.0 * N * n * n + 20.0 * N * n * 3 * np_, "GB/s", "hbm"
@@ -145,6 +152,12 @@ def kernel_rooflines(kt, steps, units, N, n, d, mode, sms, mhz, emu=False):
             work, unit, bound = accounting.tc_tile_flops(N, n), "TFLOP/s", "tensor"
             peak = pk["bf16_tflops"] * 0.5e12
             pdef = f"TF32 dense = BF16 ({pk['source']}) x 1/2 nominal ratio"
+        elif cls == "factor" and mode == "fp64" and "schur_tc" in kt:
+            # the FP64-ALU share of cyclic reduction: everything but the
+            # Schur products, which ran on the tensor cores
+            c = accounting.cr_flops(N, n, d)
+            work, unit, bound = c["factor"] + c["solve"] - accounting.tc_tile_flops(N, n), "TFLOP/s", "alu"
+            peak, pdef = fp64_peak(sms, mhz), "FP64 ALU; executed CR flops outside the Schur products"
         elif cls == "factor":
             t = accounting.thomas_flops(N, n, d)
             work, unit, bound = t["factor"] + t["solve"], "TFLOP/s", "alu"
@@ -157,7 +170,7 @@ def kernel_rooflines(kt, steps, units, N, n, d, mode, sms, mhz, emu=False):
         out[cls] = {"bound": bound, "achieved": ach / scale, "peak": peak / scale, "unit": unit,
                     "frac": ach / peak, "ms_per_unit": per * 1e3, "units_per_step": u,
                     "launches_per_step": launches / steps, "work_per_unit": work, "peak_definition": pdef}
-        if cls == "schur_tc":
+        if cls == "schur_tc" and mode != "fp64":
             out[cls]["executed_frac"] = 3 * ach / peak
     return out
 
@@ -324,7 +337,8 @@ def timed_leg(sol, call, reps, stream, max_over_ranks, N, n, d, mode, sms, mhz):
     # work units per step: one factorisation; each residual is one launch;
     # each plain refinement step is one correction
     units = {"factor": 1, "schur_tc": 1, "residual": kt.get("residual", (0, 0))[1] / reps,
-             "correction": refs[0] / reps, "slice": kt.get("slice", (0, 0))[1] / reps}
+             "correction": refs[0] / reps,
+             "slice": 1 if mode == "fp64" else kt.get("slice", (0, 0))[1] / reps}
     emu = mode != "fp64" and 64 < n <= 256 and d <= 16
     roof = kernel_rooflines(kt, reps, units, N, n, d, mode, sms, mhz, emu=emu)
     dom = max(per_step, key=lambda c: per_step[c]["ms_per_step"]) if per_step else None

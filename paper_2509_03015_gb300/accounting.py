@@ -66,6 +66,31 @@ def tc_tile_flops(N: int, n: int) -> float:
     return fl
 
 
+def emu_schur_mma_flops(N: int, n: int) -> float:
+    """BF16 tensor-core flops the FP64 tiled factorisation executes for its
+    Schur products with the digit-slice engine: per separator, 128 x 16
+    output tiles of D's lower part (one accumulation round per eliminated
+    neighbour) and of the new coupling E (one round); a round is ten
+    128 x 160 x np products (np = n rounded up to 64), one per A slice."""
+    MT, CT, np_ = -(-n // 128), -(-n // 16), -(-n // 64) * 64
+    d_tiles = sum(min(CT, (mt + 1) * 8) for mt in range(MT))
+    per_round = 2.0 * 10 * 128 * 160 * np_
+    rounds = 0
+    for Nl in levels(N)[:-1]:
+        for s in range(0, Nl, 2):
+            rounds += d_tiles * ((1 if s >= 2 else 0) + (1 if s + 1 < Nl else 0))
+            rounds += MT * CT * (1 if s + 2 < Nl else 0)
+    return rounds * per_round
+
+
+def emu_wslice_bytes(N: int, n: int) -> float:
+    """HBM bytes of the coupling-block slicing over the levels: each stored
+    n x n FP64 block read once, its ten BF16 digit planes (n x np) written."""
+    np_ = -(-n // 64) * 64
+    blocks = sum(Nl - 1 for Nl in levels(N)[:-1])
+    return blocks * (8.0 * n * n + 20.0 * n * np_)
+
+
 def segment_levels(N: int, J: int, n_star: int = 1):
     """Level sizes of the recursion with interior segments of J blocks
     (Sec. 3.1, Eq. 2-4): at a level of N_l blocks the separators sit at

@@ -88,3 +88,24 @@ def test_segment_levels():
     assert accounting.segment_levels(9, 3) == [9, 3, 1]
     assert accounting.segment_levels(9, 1) == accounting.levels(9)
     assert accounting.segment_levels(100, 1, n_star=16) == [100, 50, 25, 13]
+
+
+def test_emu_schur_mma_flops_counts_tiles_by_brute_force():
+    """Rounds of the digit-slice Schur engine: every 128 x 16 tile of D that
+    touches the lower triangle once per eliminated neighbour, every tile of E
+    once when the next separator exists; ten 128 x 160 x np products each."""
+    for N, n in [(2, 96), (3, 200), (9, 256), (64, 130)]:
+        np_ = -(-n // 64) * 64
+        tiles_lower = sum(1 for r0 in range(0, n, 128) for c0 in range(0, n, 16)
+                          if any(c <= r for r in range(r0, min(n, r0 + 128)) for c in range(c0, min(n, c0 + 16))))
+        tiles_all = len(range(0, n, 128)) * len(range(0, n, 16))
+        rounds = 0
+        for Nl in accounting.levels(N)[:-1]:
+            for s in range(0, Nl, 2):
+                rounds += tiles_lower * ((s >= 2) + (s + 1 < Nl)) + tiles_all * (s + 2 < Nl)
+        assert accounting.emu_schur_mma_flops(N, n) == rounds * 2.0 * 10 * 128 * 160 * np_
+
+
+def test_emu_wslice_bytes_one_level():
+    # N = 2: one coupling block, read as FP64 and written as ten BF16 planes
+    assert accounting.emu_wslice_bytes(2, 256) == 8.0 * 256 * 256 + 20.0 * 256 * 256
