@@ -82,6 +82,9 @@ struct bdss_ctx {
   int *Wexp = nullptr;             // (N - 1) x n row exponents
   int schur_emu_ready = 0;
   int schur_emu_on = 0;
+  // large mixed path: streamed solve passes (maps over Li and Wb)
+  CUtensorMap corr_map_li, corr_map_w;
+  int corr_ok = 0;
   bool emu_sliced = false;
   int skip_barrier = 0;
   // stats of the last call
@@ -297,6 +300,32 @@ static cudaError_t schur_emu_level(bdss_ctx *h, const Args<double> &b, int l) {
   return e;
 }
 
+// Solve pass of the large mixed path with the stored inverses, streamed: per
+// level the upward products (A2, B), the top block, then per level the
+// downward products (C), one launch each.
+static cudaError_t run_corr_passes(bdss_ctx *h, const Args<float> &b) {
+  const Plan &p = h->plan;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < p.L && e == cudaSuccess; ++l)
+    for (int sub = kSubA2; sub <= kSubB && e == cudaSuccess; ++sub) {
+      kt_begin(h, h->kt_cls);
+      e = launch_large_corr(h->corr_map_li, h->corr_map_w, b, l, sub, h->sms, h->stream);
+      kt_end(h, 1);
+      h->launches += 1;
+    }
+  kt_begin(h, h->kt_cls);
+  if (e == cudaSuccess) e = launch_large_top<float>(b, 0, h->smem, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
+    kt_begin(h, h->kt_cls);
+    e = launch_large_corr(h->corr_map_li, h->corr_map_w, b, l, kSubC, h->sms, h->stream);
+    kt_end(h, 1);
+    h->launches += 1;
+  }
+  return e;
+}
+
 // One factor and/or RHS pass over all levels, persistent or per level.
 // Large-block path: three tile sub-phases per level (see bdss_large.cu).
 template <typename T>
@@ -317,6 +346,9 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
   if (!rhs) b.d = 0;
   // solve passes with the stored inverses keep y of the eliminated blocks in Yt
   b.Yt = (!factor && inv) ? (T *)h->Yt : nullptr;
+  if constexpr (sizeof(T) == 4) {
+    if (!factor && rhs && inv && h->corr_ok && b.d <= kCorrMaxD) return run_corr_passes(h, b);
+  }
   if (h->persistent && !tc_factor && !emu_factor) {
     long long most = 1;
     for (int l = 0; l < p.L; ++l)
@@ -532,6 +564,10 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
       ok = ok && ws_alloc(h, &h->Li, (size_t)N * nn * sizeof(float));
       ok = ok && ws_alloc(h, (void **)&h->Yt, nd * sizeof(float));
       ok = ok && ws_alloc(h, (void **)&h->Ltinv, 2 * nn * sizeof(float));
+      if (ok && n % 4 == 0 && d_max <= 16 && corr_smem_bytes(n) <= (size_t)smem_optin) {
+        h->corr_ok = make_f32_map(&h->corr_map_li, (const float *)h->Li, N * n, n, n) == cudaSuccess &&
+                     make_f32_map(&h->corr_map_w, (const float *)h->Wb, (long long)slots * n, n, n) == cudaSuccess;
+      }
     }
     if (ok && h->large && d_max <= kEmuDp) {  // the tensor-core FP64 residual
       ok = ws_alloc(h, (void **)&h->emu.Aslc, emu_aslc_bytes(N, n));

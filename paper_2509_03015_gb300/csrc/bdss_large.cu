@@ -9,7 +9,6 @@
 
 namespace bdss {
 
-enum { kSubA1 = 0, kSubA2 = 1, kSubB = 2, kSubC = 3 };
 
 template <typename T, bool kTc>
 __device__ bool large_sub(const Args<T> &a, int l, int sub, bool factor, T *smem, int *s_flag, TcState *tc,
@@ -153,6 +152,386 @@ __global__ void __launch_bounds__(kThreads) k_large_top(const __grid_constant__ 
   largeTop(a, factor != 0, reinterpret_cast<double *>(smem_raw), &s_flag);
 }
 
+// ---------------------------------------------------------------------------
+// Solve passes of the mixed-precision refinement with the stored inverses,
+// streamed (FP32, n % 4 == 0, d <= 16).  Every product of a pass reads one
+// n x n FP32 block once against an n x 16 operand in shared memory, 16 FMAs
+// per matrix element, so the pass is HBM-bound: the blocks are streamed
+// through a ring of shared-memory stages filled by the TMA engine, about
+// 128 KB in flight per CTA, instead of register loads of a few KB.
+//   A2 (upward, eliminated j):  y_j = L_j^{-1} b_j        rows of L^{-1}
+//   B  (upward, separator s):   b_s -= Wt(s-1) y_{s-1} + Wt(s) y_{s+1}   rows of Wt
+//   C  (downward, eliminated j): t = y_j - Wt(j-1)^T x_{j-1} - Wt(j)^T x_{j+1},
+//                               x_j = (L_j^{-1})^T t      columns of Wt, L^{-1}
+// A row product (thread r: sum_k P[r][k] v[k]) takes chunks of 32 columns of
+// all n rows as one 2-D TMA box with the 128-byte swizzle (row r's 16-byte
+// group q sits at q ^ (r & 7)); a column product (thread r: sum_k P[k][r]
+// v[k]) takes chunks of 32 whole rows with one bulk copy.  The zeros of L^{-1}
+// above its diagonal are stored, so the triangular products run over full
+// squares.  Thread 0 refills a stage as soon as the CTA has consumed it;
+// every wait is bounded.
+// ---------------------------------------------------------------------------
+static_assert(kCorrMaxD == kRowCols, "one streamed pass carries the row tasks' 16 columns");
+constexpr int kCorrKR = 32;     // columns (row products) or rows (column products) per chunk
+constexpr int kCorrStages = 4;
+
+__host__ __device__ inline int corr_pad(int n) { return (n + kCorrKR - 1) / kCorrKR * kCorrKR; }
+__host__ __device__ inline size_t corr_stage_bytes(int n) { return (size_t)kCorrKR * n * sizeof(float); }
+// stage stride: a multiple of 1024 bytes, the period of the 128-byte swizzle
+__host__ __device__ inline size_t corr_stage_stride(int n) { return (corr_stage_bytes(n) + 1023) & ~(size_t)1023; }
+size_t corr_smem_bytes(int n) {
+  return kCorrStages * corr_stage_stride(n) + (size_t)3 * corr_pad(n) * kRowCols * sizeof(float) + 1024;
+}
+
+struct CorrProd {
+  long long row0;  // first row of the block in its buffer (block index x n)
+  int trans;       // 1: column product (bulk rows), 0: row product (2-D box)
+  int inLi;        // 1: the block is in Li, 0: in Wb
+};
+
+// Products of task t of sub-phase `sub` at level l (in consumption order).
+__device__ __forceinline__ int corr_prods(const Args<float> &a, int l, int sub, long long t, CorrProd (&P)[3]) {
+  const int n = a.p.n;
+  const long long Nl = a.p.Nl[l], off = (long long)a.p.off[l];
+  if (sub == kSubA2) {
+    P[0] = {((2 * t + 1) << l) * n, 0, 1};
+    return 1;
+  }
+  if (sub == kSubB) {
+    const long long s = 2 * t;
+    int c = 0;
+    if (s >= 2) P[c++] = {(off + s - 1) * n, 0, 0};
+    if (s + 1 < Nl) P[c++] = {(off + s) * n, 0, 0};
+    return c;
+  }
+  const long long j = 2 * t + 1;
+  int c = 0;
+  P[c++] = {(off + j - 1) * n, 1, 0};
+  if (j + 1 < Nl) P[c++] = {(off + j) * n, 1, 0};
+  P[c++] = {(j << l) * n, 1, 1};
+  return c;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// acc[c] += sum over the 32 columns k0.. of row r of a swizzled box.
+__device__ __forceinline__ void corr_rows_chunk(const unsigned char *stage, int r, int k0, const float *V,
+                                                float (&acc)[kRowCols]) {
+  const unsigned char *row = stage + (size_t)r * 128;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 f = *reinterpret_cast<const float4 *>(row + ((q ^ (r & 7)) << 4));
+    const float fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float4 *v4 = reinterpret_cast<const float4 *>(V + (size_t)(k0 + 4 * q + e) * kRowCols);
+#pragma unroll
+      for (int c4 = 0; c4 < kRowCols / 4; ++c4) {
+        const float4 w = v4[c4];
+        acc[4 * c4 + 0] = fmaf(fv[e], w.x, acc[4 * c4 + 0]);
+        acc[4 * c4 + 1] = fmaf(fv[e], w.y, acc[4 * c4 + 1]);
+        acc[4 * c4 + 2] = fmaf(fv[e], w.z, acc[4 * c4 + 2]);
+        acc[4 * c4 + 3] = fmaf(fv[e], w.w, acc[4 * c4 + 3]);
+      }
+    }
+  }
+}
+
+// acc[c] += sum over the `rows` rows k0.. of column r of a row chunk.
+__device__ __forceinline__ void corr_cols_chunk(const float *stage, int n, int r, int k0, int rows, const float *V,
+                                                float (&acc)[kRowCols]) {
+#pragma unroll 4
+  for (int kk = 0; kk < rows; ++kk) {
+    const float p = stage[(size_t)kk * n + r];
+    const float4 *v4 = reinterpret_cast<const float4 *>(V + (size_t)(k0 + kk) * kRowCols);
+#pragma unroll
+    for (int c4 = 0; c4 < kRowCols / 4; ++c4) {
+      const float4 w = v4[c4];
+      acc[4 * c4 + 0] = fmaf(p, w.x, acc[4 * c4 + 0]);
+      acc[4 * c4 + 1] = fmaf(p, w.y, acc[4 * c4 + 1]);
+      acc[4 * c4 + 2] = fmaf(p, w.z, acc[4 * c4 + 2]);
+      acc[4 * c4 + 3] = fmaf(p, w.w, acc[4 * c4 + 3]);
+    }
+  }
+}
+
+// sV[k][c] = src[k][c] for k < n, c < d; zero elsewhere (rows up to the pad).
+template <typename S>
+__device__ __forceinline__ void corr_stage_vec(float *sV, const S *src, int n, int np, int d) {
+#pragma unroll 4
+  for (int e = threadIdx.x; e < np * kRowCols; e += blockDim.x) {
+    const int k = e / kRowCols, c = e - k * kRowCols;
+    sV[e] = (k < n && c < d) ? (float)ldcg(src + (size_t)k * d + c) : 0.0f;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_large_corr(const __grid_constant__ CUtensorMap mapLi, const __grid_constant__ CUtensorMap mapW,
+                 const __grid_constant__ Args<float> a, int l, int sub) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t full[kCorrStages], vbar;
+  __shared__ int s_ok;
+  // one read of the status decides for the whole CTA
+  if (threadIdx.x == 0) s_ok = ld_relaxed_i32(&a.st->status) == 0;
+  __syncthreads();
+  if (!s_ok) return;
+  const int n = a.p.n, d = a.d, r = threadIdx.x, np = corr_pad(n);
+  const long long Nl = a.p.Nl[l];
+  const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2;
+  const size_t SB = corr_stage_bytes(n), SS = corr_stage_stride(n), nd = (size_t)n * d;
+  const int nch = (n + kCorrKR - 1) / kCorrKR;
+  // 1024-byte aligned ring, by pointer arithmetic on the shared array so that
+  // the compiler keeps shared-memory loads (an integer round trip would make
+  // every read below a generic load)
+  unsigned char *ring = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float *sV0 = reinterpret_cast<float *>(ring + kCorrStages * SS);
+  float *sV1 = sV0 + (size_t)np * kRowCols, *sV2 = sV1 + (size_t)np * kRowCols;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kCorrStages; ++s) mbar_init(&full[s], 1);
+    mbar_init(&vbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // producer cursor (thread 0): task pt, product pp, chunk pc
+  long long pt = blockIdx.x;
+  int pp = 0, pc = 0, pn = 0;
+  CorrProd PP[3];
+  long long issued = 0;
+  auto issue = [&](int stage) {
+    while (pt < tasks && pp >= pn) {
+      pt += gridDim.x;
+      pp = 0;
+      pc = 0;
+      pn = pt < tasks ? corr_prods(a, l, sub, pt, PP) : 0;
+    }
+    if (pt >= tasks) return;
+    const CorrProd &P = PP[pp];
+    unsigned char *dst = ring + (size_t)stage * SS;
+    if (!P.trans) {
+      mbar_expect_tx(&full[stage], (uint32_t)SB);
+      tma_load_2d(dst, P.inLi ? &mapLi : &mapW, pc * kCorrKR, (int)P.row0, &full[stage]);
+    } else {
+      const int rows = min(kCorrKR, n - pc * kCorrKR);
+      const uint32_t bytes = (uint32_t)((size_t)rows * n * sizeof(float));
+      const float *src = (P.inLi ? a.Li : a.Wb) + (size_t)(P.row0 + (long long)pc * kCorrKR) * n;
+      mbar_expect_tx(&full[stage], bytes);
+      bulk_load(dst, src, bytes, &full[stage]);
+    }
+    ++issued;
+    if (++pc == nch) {
+      pc = 0;
+      ++pp;
+    }
+  };
+  if (threadIdx.x == 0) {
+    pn = pt < tasks ? corr_prods(a, l, sub, pt, PP) : 0;
+    for (int s = 0; s < kCorrStages; ++s) issue(s);
+  }
+  bool vpend = false;  // an operand copy may still be in flight (timeout path)
+  int cs = 0;
+  uint32_t cph = 0, vph = 0;
+  long long consumed = 0;
+  bool ok = true;
+  const float *ys = a.Yt ? a.Yt : a.Y;  // y of the eliminated blocks in this pass
+  // rows n .. np - 1 of the operands stay zero (only rows < n are written)
+  for (int e = n * kRowCols + threadIdx.x; e < np * kRowCols; e += blockDim.x) sV0[e] = sV1[e] = sV2[e] = 0.0f;
+  // with 16 columns an operand block is n x 16 contiguous floats: one bulk copy
+  const bool bulkV = (d == kRowCols);
+  const uint32_t vbytes = (uint32_t)((size_t)n * kRowCols * sizeof(float));
+  for (long long t = blockIdx.x; t < tasks && ok; t += gridDim.x) {
+    long long orig;
+    bool hasM = false;
+    int npr;
+    const float *src0 = nullptr, *src1 = nullptr, *src2 = nullptr;
+    const double *src0d = nullptr;
+    if (sub == kSubA2) {
+      orig = (2 * t + 1) << l;
+      const size_t bo = (size_t)orig * nd;
+      if (l == 0 && a.B64) src0d = a.B64 + bo;
+      else src0 = ((l == 0 && a.Bt) ? a.Bt : a.Y) + bo;
+      npr = 1;
+    } else if (sub == kSubB) {
+      const long long s = 2 * t;
+      orig = s << l;
+      hasM = s >= 2;
+      const bool hasP = s + 1 < Nl;
+      if (hasM) src0 = ys + (size_t)((s - 1) << l) * nd;
+      if (hasP) src1 = ys + (size_t)((s + 1) << l) * nd;
+      npr = (int)hasM + (int)hasP;
+    } else {
+      const long long j = 2 * t + 1;
+      orig = j << l;
+      const bool hasR = j + 1 < Nl;
+      src0 = a.Y + (size_t)((j - 1) << l) * nd;
+      if (hasR) src1 = a.Y + (size_t)((j + 1) << l) * nd;
+      src2 = ys + (size_t)orig * nd;  // y_j, turned into t in place
+      npr = hasR ? 3 : 2;
+    }
+    const uint32_t nsrc = (src0 ? 1u : 0u) + (src1 ? 1u : 0u) + (src2 ? 1u : 0u);
+    if (bulkV && !src0d) {
+      if (nsrc > 0) {
+        if (threadIdx.x == 0) {
+          fence_proxy_async_smem();
+          mbar_expect_tx(&vbar, nsrc * vbytes);
+          if (src0) bulk_load(sV0, src0, vbytes, &vbar);
+          if (src1) bulk_load(sV1, src1, vbytes, &vbar);
+          if (src2) bulk_load(sV2, src2, vbytes, &vbar);
+        }
+        if (!mbar_wait_cta(&vbar, vph, a.timeout_ns, &s_ok)) {
+          if (threadIdx.x == 0) set_status(a.st, kStTimeout, l, -1);
+          vpend = true;
+          ok = false;
+          break;
+        }
+        vph ^= 1;
+      }
+    } else {
+      if (src0d) corr_stage_vec(sV0, src0d, n, np, d);
+      if (src0) corr_stage_vec(sV0, src0, n, np, d);
+      if (src1) corr_stage_vec(sV1, src1, n, np, d);
+      if (src2) corr_stage_vec(sV2, src2, n, np, d);
+      __syncthreads();
+    }
+    float acc[kRowCols];
+#pragma unroll
+    for (int c = 0; c < kRowCols; ++c) acc[c] = 0.0f;
+    for (int p = 0; p < npr && ok; ++p) {
+      const bool lastC = (sub == kSubC && p == npr - 1);
+      if (lastC) {
+        // t = y_j - (W_L x_{j-1} + W_R x_{j+1}): thread r updates its own row
+        if (r < n) {
+#pragma unroll
+          for (int c = 0; c < kRowCols; ++c) sV2[r * kRowCols + c] -= acc[c];
+        }
+#pragma unroll
+        for (int c = 0; c < kRowCols; ++c) acc[c] = 0.0f;
+        __syncthreads();
+      }
+      const float *V = (sub == kSubA2)   ? sV0
+                       : (sub == kSubB) ? ((p == 0 && hasM) ? sV0 : sV1)
+                       : lastC          ? sV2
+                                        : (p == 0 ? sV0 : sV1);
+      for (int c = 0; c < nch; ++c) {
+        if (!mbar_wait_cta(&full[cs], cph, a.timeout_ns, &s_ok)) {
+          if (threadIdx.x == 0) set_status(a.st, kStTimeout, l, -1);
+          ok = false;
+          break;
+        }
+        const unsigned char *stage = ring + (size_t)cs * SS;
+        if (r < n) {
+          if (sub == kSubC)
+            corr_cols_chunk(reinterpret_cast<const float *>(stage), n, r, c * kCorrKR, min(kCorrKR, n - c * kCorrKR),
+                            V, acc);
+          else
+            corr_rows_chunk(stage, r, c * kCorrKR, V, acc);
+        }
+        __syncthreads();  // every thread is done with the stage
+        ++consumed;
+        if (threadIdx.x == 0) {
+          fence_proxy_async_smem();
+          issue(cs);
+        }
+        if (++cs == kCorrStages) {
+          cs = 0;
+          cph ^= 1;
+        }
+      }
+    }
+    if (!ok || r >= n) continue;
+    const size_t o = (size_t)orig * nd + (size_t)r * d;
+    if (d == kRowCols) {
+      // a thread's row of the block is 16 contiguous values
+      if (sub == kSubA2) {
+        float4 *dst = reinterpret_cast<float4 *>(a.Yt + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+      } else if (sub == kSubB) {
+        float base[kRowCols];
+        if (l == 0 && a.B64) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const double2 b2 = __ldcg(reinterpret_cast<const double2 *>(a.B64 + o) + q);
+            base[2 * q] = (float)b2.x;
+            base[2 * q + 1] = (float)b2.y;
+          }
+        } else {
+          const float *bs = (l == 0 && a.Bt) ? a.Bt : a.Y;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 b4 = __ldcg(reinterpret_cast<const float4 *>(bs + o) + q);
+            base[4 * q] = b4.x;
+            base[4 * q + 1] = b4.y;
+            base[4 * q + 2] = b4.z;
+            base[4 * q + 3] = b4.w;
+          }
+        }
+        float4 *dst = reinterpret_cast<float4 *>(a.Y + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          dst[q] = make_float4(base[4 * q] - acc[4 * q], base[4 * q + 1] - acc[4 * q + 1],
+                               base[4 * q + 2] - acc[4 * q + 2], base[4 * q + 3] - acc[4 * q + 3]);
+      } else {
+        float4 *dst = reinterpret_cast<float4 *>(a.Y + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        if (a.X64) {
+          double2 *x2 = reinterpret_cast<double2 *>(a.X64 + o);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            double2 v = make_double2((double)acc[2 * q], (double)acc[2 * q + 1]);
+            if (a.x_accumulate) {
+              const double2 old = x2[q];
+              v.x += old.x;
+              v.y += old.y;
+            }
+            x2[q] = v;
+          }
+        }
+      }
+    } else if (sub == kSubA2) {
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c < d) a.Yt[o + c] = acc[c];
+    } else if (sub == kSubB) {
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c < d) {
+          float base;
+          if (l == 0 && a.B64) base = (float)ldcg(a.B64 + o + c);
+          else if (l == 0 && a.Bt) base = ldcg(a.Bt + o + c);
+          else base = ldcg(a.Y + o + c);
+          a.Y[o + c] = base - acc[c];
+        }
+    } else {
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c < d) {
+          a.Y[o + c] = acc[c];
+          if (a.X64) a.X64[o + c] = a.x_accumulate ? a.X64[o + c] + (double)acc[c] : (double)acc[c];
+        }
+    }
+  }
+  // after a timeout: wait out the copies still in flight before the CTA ends
+  if (threadIdx.x == 0 && vpend) mbar_wait(&vbar, vph, a.timeout_ns);
+  if (threadIdx.x == 0 && issued > consumed) {
+    int s = cs;
+    uint32_t ph = cph;
+    for (long long k = consumed; k < issued; ++k) {
+      mbar_wait(&full[s], ph, a.timeout_ns);
+      if (++s == kCorrStages) {
+        s = 0;
+        ph ^= 1;
+      }
+    }
+  }
+}
+
 // FP64 residual for large blocks: one CTA per block row, one thread per row r
 // of the block with up to 16 right-hand-side columns in registers:
 //   R[r][c] = B[r][c] - 0.5 sum_p (A[r][p] + A[p][r]) x_i[p][c]
@@ -253,7 +632,7 @@ cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm, int 
   const void *kernels[] = {(const void *)k_large_persistent<T, false>, (const void *)k_large_sub<T, false>,
                            (const void *)k_large_persistent<float, true>, (const void *)k_large_sub<float, true>,
                            (const void *)k_large_top<T>, (const void *)k_residual_rows,
-                           (const void *)k_tc_selftest};
+                           (const void *)k_tc_selftest, (const void *)k_large_corr};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -309,6 +688,16 @@ cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStre
   return cudaGetLastError();
 }
 
+cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW, const Args<float> &a, int l,
+                              int sub, int sms, cudaStream_t s) {
+  const long long Nl = a.p.Nl[l];
+  const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2;
+  if (tasks <= 0) return cudaSuccess;
+  const int grid = (int)(tasks < sms ? tasks : sms);
+  k_large_corr<<<grid, kThreads, corr_smem_bytes(a.p.n), s>>>(mapLi, mapW, a, l, sub);
+  return cudaGetLastError();
+}
+
 long long large_sub_tasks(const Plan &p, int l, int sub, int factor, int d, int esz, int tf32, int inv) {
   const long long Nl = p.Nl[l], nE = Nl / 2, nS = (Nl + 1) / 2;
   if (sub == kSubBRhsOnly) return nS * largeB_tiles(p.n, false, d);
@@ -329,7 +718,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, int n, int box_rows);
 cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows, int n) {
+  return make_f32_map(out, Wb, rows, n, kTcM);
+}
+
+// 2-D map over `rows` rows of n floats: boxes of 32 columns x box_rows rows,
+// 128-byte swizzle.
+cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, int n, int box_rows) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -341,9 +737,9 @@ cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows,
   }
   const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)Wb, dims, strides, box, estr,
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

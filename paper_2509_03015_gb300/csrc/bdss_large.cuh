@@ -20,6 +20,15 @@
 
 namespace bdss {
 
+// A pointer into the dynamic shared memory, re-derived from the shared array
+// itself: inside a function that is not inlined a pointer parameter is
+// generic, and every access through it would be a generic load or store.
+template <typename T>
+__device__ __forceinline__ T *as_shared(T *p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  return reinterpret_cast<T *>(smem_raw + (smem_u32(p) - smem_u32(smem_raw)));
+}
+
 constexpr int kTile = 64;   // output / triangular tile
 constexpr int kKc = 32;     // k-chunk staged per gemm step
 constexpr int kTilePad = kTile + 1;
@@ -165,6 +174,8 @@ __host__ __device__ inline size_t smem_large(int n, int d, int esz) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __noinline__ int chol_blocked(T *M, int n, const double *src_sym, T *smem, int *s_flag, T *Dinv = nullptr) {
+  smem = as_shared(smem);
+  s_flag = as_shared(s_flag);
   const int nt = ntiles(n);
   T *sT = smem;                              // 64 x 65 tile
   T *sA = sT + kTile * kTilePad;
@@ -847,6 +858,8 @@ __device__ void largeC(const Args<T> &a, int l, long long j, T *smem) {
 // blocked Cholesky in place, then x_0 = L^{-T} L^{-1} b_0.
 template <typename T>
 __device__ __noinline__ bool largeTop(const Args<T> &a, bool factor, double *smem, int *s_flag) {
+  smem = as_shared(smem);
+  s_flag = as_shared(s_flag);
   const int n = a.p.n, d = a.d, L = a.p.L, lv = n + 1;
   const size_t nn = (size_t)n * n;
   if (factor) {

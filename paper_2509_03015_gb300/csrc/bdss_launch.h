@@ -42,6 +42,20 @@ cudaError_t launch_large_sub(const Args<T> &a, int l, int sub, int factor, int g
 template <typename T> cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStream_t s);
 // Tasks of sub-phase `sub` at level l; inv = the pass uses the stored
 // inverses (FP32 tiled path).
+// Sub-phases of a level of the large path (bdss_large.cu): A1 Cholesky per
+// eliminated block, A2 forward substitution, B separator (Schur) update,
+// C downward back-substitution.
+constexpr int kSubA1 = 0, kSubA2 = 1, kSubB = 2, kSubC = 3;
+
+// Streamed solve passes of the large FP32 path with the stored inverses
+// (n % 4 == 0, d <= 16): sub-phases kSubA2 (1), kSubB (2), kSubC (3) of level
+// l as one launch each (bdss_large.cu).
+constexpr int kCorrMaxD = 16;  // right-hand-side columns of one streamed pass
+size_t corr_smem_bytes(int n);
+cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, int n, int box_rows);
+cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW, const Args<float> &a, int l,
+                              int sub, int sms, cudaStream_t s);
+
 // Sub-phase code of the large path: the separators' RHS tiles alone (their D
 // and E tiles ran elsewhere, e.g. on the tensor cores).
 constexpr int kSubBRhsOnly = 4;

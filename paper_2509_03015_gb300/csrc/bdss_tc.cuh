@@ -237,8 +237,9 @@ __device__ __forceinline__ void tc_read_row(const TcState &s, float (&v)[64], in
 // the dynamic shared memory cannot clobber them) and TMEM (warp 0
 // allocates); call with all threads.
 __device__ __forceinline__ void tc_begin(TcState &s, unsigned char *smem_base, uint64_t *bars, uint32_t *tmem_slot) {
-  const uintptr_t p = (reinterpret_cast<uintptr_t>(smem_base) + 1023) & ~(uintptr_t)1023;
-  s.slab = reinterpret_cast<unsigned char *>(p);
+  // aligned by pointer arithmetic, which keeps the slab reads of the split
+  // shared-memory accesses (an integer round trip makes them generic)
+  s.slab = smem_base + ((1024u - (smem_u32(smem_base) & 1023u)) & 1023u);
   s.bar_tma = bars;
   s.bar_mma = bars + 1;
   s.s_ok = reinterpret_cast<int *>(bars + 2);
