@@ -173,15 +173,19 @@ __global__ void __launch_bounds__(kThreads) k_large_top(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 static_assert(kCorrMaxD == kRowCols, "one streamed pass carries the row tasks' 16 columns");
 constexpr int kCorrKR = 32;     // columns (row products) or rows (column products) per chunk
-constexpr int kCorrStages = 4;
+constexpr int kCorrStages = 4;  // ring depth with one CTA per SM (levels with few blocks)
+constexpr int kCorrStagesPair = 2;  // ring depth with two CTAs per SM (levels with many blocks)
+constexpr size_t kCorrSmemPerSM = 233472;  // shared memory of an SM (bytes)
 
 __host__ __device__ inline int corr_pad(int n) { return (n + kCorrKR - 1) / kCorrKR * kCorrKR; }
 __host__ __device__ inline size_t corr_stage_bytes(int n) { return (size_t)kCorrKR * n * sizeof(float); }
 // stage stride: a multiple of 1024 bytes, the period of the 128-byte swizzle
 __host__ __device__ inline size_t corr_stage_stride(int n) { return (corr_stage_bytes(n) + 1023) & ~(size_t)1023; }
-size_t corr_smem_bytes(int n) {
-  return kCorrStages * corr_stage_stride(n) + (size_t)3 * corr_pad(n) * kRowCols * sizeof(float) + 1024;
+size_t corr_smem_bytes(int n, int stages, int q) {
+  return stages * corr_stage_stride(n) + (size_t)2 * corr_pad(n) * kRowCols * sizeof(float) +
+         (size_t)(q - 1) * kThreads * kRowCols * sizeof(float) + 1024;
 }
+size_t corr_smem_bytes(int n) { return corr_smem_bytes(n, kCorrStages, 2); }
 
 struct CorrProd {
   long long row0;  // first row of the block in its buffer (block index x n)
@@ -219,12 +223,15 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       : "memory");
 }
 
-// acc[c] += sum over the 32 columns k0.. of row r of a swizzled box.
-__device__ __forceinline__ void corr_rows_chunk(const unsigned char *stage, int r, int k0, const float *V,
+// acc[c] += sum over the columns k0 + 4 q0 .. k0 + 4 (q0 + kG) - 1 of row r of
+// a swizzled box of 32 columns (kG of its eight 16-byte groups).
+template <int kG>
+__device__ __forceinline__ void corr_rows_chunk(const unsigned char *stage, int r, int k0, int q0, const float *V,
                                                 float (&acc)[kRowCols]) {
   const unsigned char *row = stage + (size_t)r * 128;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int i = 0; i < kG; ++i) {
+    const int q = q0 + i;
     const float4 f = *reinterpret_cast<const float4 *>(row + ((q ^ (r & 7)) << 4));
     const float fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
@@ -242,11 +249,11 @@ __device__ __forceinline__ void corr_rows_chunk(const unsigned char *stage, int 
   }
 }
 
-// acc[c] += sum over the `rows` rows k0.. of column r of a row chunk.
-__device__ __forceinline__ void corr_cols_chunk(const float *stage, int n, int r, int k0, int rows, const float *V,
-                                                float (&acc)[kRowCols]) {
+// acc[c] += sum over the rows kk0 .. kk1 - 1 (k0 + kk) of column r of a row chunk.
+__device__ __forceinline__ void corr_cols_chunk(const float *stage, int n, int r, int k0, int kk0, int kk1,
+                                                const float *V, float (&acc)[kRowCols]) {
 #pragma unroll 4
-  for (int kk = 0; kk < rows; ++kk) {
+  for (int kk = kk0; kk < kk1; ++kk) {
     const float p = stage[(size_t)kk * n + r];
     const float4 *v4 = reinterpret_cast<const float4 *>(V + (size_t)(k0 + kk) * kRowCols);
 #pragma unroll
@@ -270,9 +277,39 @@ __device__ __forceinline__ void corr_stage_vec(float *sV, const S *src, int n, i
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// With kQ threads per output row (each on 32 / kQ columns or rows of every
+// chunk), the partial sums meet in shared memory in a fixed order: thread
+// kq = 0 adds those of kq = 1, 2, ...  All threads call it.
+template <int kQ>
+__device__ __forceinline__ void corr_reduce(float (&acc)[kRowCols], float *red, int rl, int kq) {
+  if constexpr (kQ > 1) {
+    if (kq > 0) {
+      float4 *dst = reinterpret_cast<float4 *>(red + ((size_t)(kq - 1) * kThreads + rl) * kRowCols);
+#pragma unroll
+      for (int q = 0; q < kRowCols / 4; ++q) dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    __syncthreads();
+    if (kq == 0) {
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) {
+        const float4 *src = reinterpret_cast<const float4 *>(red + ((size_t)(i - 1) * kThreads + rl) * kRowCols);
+#pragma unroll
+        for (int q = 0; q < kRowCols / 4; ++q) {
+          const float4 v = src[q];
+          acc[4 * q] += v.x;
+          acc[4 * q + 1] += v.y;
+          acc[4 * q + 2] += v.z;
+          acc[4 * q + 3] += v.w;
+        }
+      }
+    }
+  }
+}
+
+template <int kQ>
+__global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
     k_large_corr(const __grid_constant__ CUtensorMap mapLi, const __grid_constant__ CUtensorMap mapW,
-                 const __grid_constant__ Args<float> a, int l, int sub) {
+                 const __grid_constant__ Args<float> a, int l, int sub, int stages) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t full[kCorrStages], vbar;
   __shared__ int s_ok;
@@ -280,7 +317,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) s_ok = ld_relaxed_i32(&a.st->status) == 0;
   __syncthreads();
   if (!s_ok) return;
-  const int n = a.p.n, d = a.d, r = threadIdx.x, np = corr_pad(n);
+  const int n = a.p.n, d = a.d, np = corr_pad(n);
+  // thread = (row or column r of the block, share kq of every chunk)
+  const int r = threadIdx.x % kThreads, kq = threadIdx.x / kThreads;
+  const bool active = r < n;
   const long long Nl = a.p.Nl[l];
   const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2;
   const size_t SB = corr_stage_bytes(n), SS = corr_stage_stride(n), nd = (size_t)n * d;
@@ -289,10 +329,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the compiler keeps shared-memory loads (an integer round trip would make
   // every read below a generic load)
   unsigned char *ring = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  float *sV0 = reinterpret_cast<float *>(ring + kCorrStages * SS);
-  float *sV1 = sV0 + (size_t)np * kRowCols, *sV2 = sV1 + (size_t)np * kRowCols;
+  float *sV0 = reinterpret_cast<float *>(ring + stages * SS);
+  float *sV1 = sV0 + (size_t)np * kRowCols;
+  float *red = sV1 + (size_t)np * kRowCols;  // (kQ - 1) x 256 x 16 partial sums
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kCorrStages; ++s) mbar_init(&full[s], 1);
+    for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
     mbar_init(&vbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -331,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
   if (threadIdx.x == 0) {
     pn = pt < tasks ? corr_prods(a, l, sub, pt, PP) : 0;
-    for (int s = 0; s < kCorrStages; ++s) issue(s);
+    for (int s = 0; s < stages; ++s) issue(s);
   }
   bool vpend = false;  // an operand copy may still be in flight (timeout path)
   int cs = 0;
@@ -340,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool ok = true;
   const float *ys = a.Yt ? a.Yt : a.Y;  // y of the eliminated blocks in this pass
   // rows n .. np - 1 of the operands stay zero (only rows < n are written)
-  for (int e = n * kRowCols + threadIdx.x; e < np * kRowCols; e += blockDim.x) sV0[e] = sV1[e] = sV2[e] = 0.0f;
+  for (int e = n * kRowCols + threadIdx.x; e < np * kRowCols; e += blockDim.x) sV0[e] = sV1[e] = 0.0f;
   // with 16 columns an operand block is n x 16 contiguous floats: one bulk copy
   const bool bulkV = (d == kRowCols);
   const uint32_t vbytes = (uint32_t)((size_t)n * kRowCols * sizeof(float));
@@ -348,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     long long orig;
     bool hasM = false;
     int npr;
-    const float *src0 = nullptr, *src1 = nullptr, *src2 = nullptr;
+    const float *src0 = nullptr, *src1 = nullptr, *yj = nullptr;
     const double *src0d = nullptr;
     if (sub == kSubA2) {
       orig = (2 * t + 1) << l;
@@ -370,10 +411,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool hasR = j + 1 < Nl;
       src0 = a.Y + (size_t)((j - 1) << l) * nd;
       if (hasR) src1 = a.Y + (size_t)((j + 1) << l) * nd;
-      src2 = ys + (size_t)orig * nd;  // y_j, turned into t in place
+      yj = ys + (size_t)orig * nd;  // y_j: read at the t step, fetched into L2 now
+      if (active && kq == 0) prefetch_l2(yj + (size_t)r * d, (size_t)d * sizeof(float));
       npr = hasR ? 3 : 2;
     }
-    const uint32_t nsrc = (src0 ? 1u : 0u) + (src1 ? 1u : 0u) + (src2 ? 1u : 0u);
+    const uint32_t nsrc = (src0 ? 1u : 0u) + (src1 ? 1u : 0u);
     if (bulkV && !src0d) {
       if (nsrc > 0) {
         if (threadIdx.x == 0) {
@@ -381,7 +423,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_expect_tx(&vbar, nsrc * vbytes);
           if (src0) bulk_load(sV0, src0, vbytes, &vbar);
           if (src1) bulk_load(sV1, src1, vbytes, &vbar);
-          if (src2) bulk_load(sV2, src2, vbytes, &vbar);
         }
         if (!mbar_wait_cta(&vbar, vph, a.timeout_ns, &s_ok)) {
           if (threadIdx.x == 0) set_status(a.st, kStTimeout, l, -1);
@@ -395,7 +436,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (src0d) corr_stage_vec(sV0, src0d, n, np, d);
       if (src0) corr_stage_vec(sV0, src0, n, np, d);
       if (src1) corr_stage_vec(sV1, src1, n, np, d);
-      if (src2) corr_stage_vec(sV2, src2, n, np, d);
       __syncthreads();
     }
     float acc[kRowCols];
@@ -404,10 +444,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int p = 0; p < npr && ok; ++p) {
       const bool lastC = (sub == kSubC && p == npr - 1);
       if (lastC) {
-        // t = y_j - (W_L x_{j-1} + W_R x_{j+1}): thread r updates its own row
-        if (r < n) {
+        // t = y_j - (W_L x_{j-1} + W_R x_{j+1}) into sV0, free once the W
+        // products are done (the last chunk ended with a barrier)
+        corr_reduce<kQ>(acc, red, r, kq);
+        if (active && kq == 0) {
+          const float *yr = yj + (size_t)r * d;
+          if (d == kRowCols) {
 #pragma unroll
-          for (int c = 0; c < kRowCols; ++c) sV2[r * kRowCols + c] -= acc[c];
+            for (int q = 0; q < 4; ++q) {
+              const float4 y4 = __ldcg(reinterpret_cast<const float4 *>(yr) + q);
+              sV0[r * kRowCols + 4 * q + 0] = y4.x - acc[4 * q + 0];
+              sV0[r * kRowCols + 4 * q + 1] = y4.y - acc[4 * q + 1];
+              sV0[r * kRowCols + 4 * q + 2] = y4.z - acc[4 * q + 2];
+              sV0[r * kRowCols + 4 * q + 3] = y4.w - acc[4 * q + 3];
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < kRowCols; ++c) sV0[r * kRowCols + c] = (c < d) ? ldcg(yr + c) - acc[c] : 0.0f;
+          }
         }
 #pragma unroll
         for (int c = 0; c < kRowCols; ++c) acc[c] = 0.0f;
@@ -415,8 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const float *V = (sub == kSubA2)   ? sV0
                        : (sub == kSubB) ? ((p == 0 && hasM) ? sV0 : sV1)
-                       : lastC          ? sV2
-                                        : (p == 0 ? sV0 : sV1);
+                       : (lastC || p == 0) ? sV0
+                                           : sV1;
       for (int c = 0; c < nch; ++c) {
         if (!mbar_wait_cta(&full[cs], cph, a.timeout_ns, &s_ok)) {
           if (threadIdx.x == 0) set_status(a.st, kStTimeout, l, -1);
@@ -424,12 +478,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         const unsigned char *stage = ring + (size_t)cs * SS;
-        if (r < n) {
-          if (sub == kSubC)
-            corr_cols_chunk(reinterpret_cast<const float *>(stage), n, r, c * kCorrKR, min(kCorrKR, n - c * kCorrKR),
-                            V, acc);
-          else
-            corr_rows_chunk(stage, r, c * kCorrKR, V, acc);
+        if (active) {
+          if (sub == kSubC) {
+            const int rows = min(kCorrKR, n - c * kCorrKR), per = kCorrKR / kQ;
+            corr_cols_chunk(reinterpret_cast<const float *>(stage), n, r, c * kCorrKR, kq * per,
+                            min(rows, (kq + 1) * per), V, acc);
+          } else {
+            corr_rows_chunk<8 / kQ>(stage, r, c * kCorrKR, kq * (8 / kQ), V, acc);
+          }
         }
         __syncthreads();  // every thread is done with the stage
         ++consumed;
@@ -437,13 +493,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_proxy_async_smem();
           issue(cs);
         }
-        if (++cs == kCorrStages) {
+        if (++cs == stages) {
           cs = 0;
           cph ^= 1;
         }
       }
     }
-    if (!ok || r >= n) continue;
+    if (!ok) continue;
+    corr_reduce<kQ>(acc, red, r, kq);
+    if (!active || kq != 0) continue;
     const size_t o = (size_t)orig * nd + (size_t)r * d;
     if (d == kRowCols) {
       // a thread's row of the block is 16 contiguous values
@@ -524,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t ph = cph;
     for (long long k = consumed; k < issued; ++k) {
       mbar_wait(&full[s], ph, a.timeout_ns);
-      if (++s == kCorrStages) {
+      if (++s == stages) {
         s = 0;
         ph ^= 1;
       }
@@ -632,7 +690,8 @@ cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm, int 
   const void *kernels[] = {(const void *)k_large_persistent<T, false>, (const void *)k_large_sub<T, false>,
                            (const void *)k_large_persistent<float, true>, (const void *)k_large_sub<float, true>,
                            (const void *)k_large_top<T>, (const void *)k_residual_rows,
-                           (const void *)k_tc_selftest, (const void *)k_large_corr};
+                           (const void *)k_tc_selftest, (const void *)k_large_corr<1>,
+                           (const void *)k_large_corr<2>};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -693,8 +752,19 @@ cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW,
   const long long Nl = a.p.Nl[l];
   const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2;
   if (tasks <= 0) return cudaSuccess;
-  const int grid = (int)(tasks < sms ? tasks : sms);
-  k_large_corr<<<grid, kThreads, corr_smem_bytes(a.p.n), s>>>(mapLi, mapW, a, l, sub);
+  // many blocks: two CTAs per SM with a two-stage ring each (more warps to
+  // hide latency, the same bytes in flight); few blocks: one CTA per block
+  // with a deeper ring
+  //   few blocks: one CTA per block, two threads per row, a deeper ring
+  const bool pair = tasks >= 2LL * sms && 2 * (corr_smem_bytes(a.p.n, kCorrStagesPair, 1) + 1024) <= kCorrSmemPerSM;
+  const long long cap = pair ? 2LL * sms : (long long)sms;
+  const int grid = (int)(tasks < cap ? tasks : cap);
+  if (pair)
+    k_large_corr<1><<<grid, kThreads, corr_smem_bytes(a.p.n, kCorrStagesPair, 1), s>>>(mapLi, mapW, a, l, sub,
+                                                                                      kCorrStagesPair);
+  else
+    k_large_corr<2><<<grid, 2 * kThreads, corr_smem_bytes(a.p.n, kCorrStages, 2), s>>>(mapLi, mapW, a, l, sub,
+                                                                                      kCorrStages);
   return cudaGetLastError();
 }
 

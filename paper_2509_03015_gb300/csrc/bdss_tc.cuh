@@ -36,8 +36,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 }
 // Bounded wait for the phase with the given parity.  Returns false when the
 // limit is reached (the caller records a timeout).
+// The clock is read only once the phase is late (after 64 failed polls): a
+// wait that succeeds at once, the common case, costs no timer read.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long timeout_ns) {
-  const long long t0 = global_ns();
+  long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t done;
     asm volatile(
@@ -46,7 +48,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 63) == 63 && global_ns() - t0 > timeout_ns) return false;
+    if ((it & 63) == 63) {
+      const long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > timeout_ns) return false;
+    }
   }
 }
 
