@@ -85,6 +85,9 @@ struct bdss_ctx {
   // large mixed path: streamed solve passes (maps over Li and Wb)
   CUtensorMap corr_map_li, corr_map_w;
   int corr_ok = 0;
+  // TF32 mode: the pipelined 3xTF32 Schur tiles read W through this map
+  CUtensorMap ts_map_w;
+  int ts_ok = 0;
   bool emu_sliced = false;
   int skip_barrier = 0;
   // stats of the last call
@@ -326,6 +329,28 @@ static cudaError_t run_corr_passes(bdss_ctx *h, const Args<float> &b) {
   return e;
 }
 
+// Separator update of level l in the TF32 mode: the D and E tiles on the
+// pipelined tensor-core kernel, then the separators' RHS tiles on the ALU.
+static cudaError_t schur_tf32_level(bdss_ctx *h, const Args<float> &b, int l) {
+  const Plan &p = h->plan;
+  kt_begin(h, BDSS_KT_SCHUR_TC);
+  cudaError_t e = launch_tf32_schur(h->ts_map_w, b, l, h->sms, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  if (e != cudaSuccess || b.d == 0) return e;
+  kt_begin(h, h->kt_cls);
+  // b_s -= W^T y of the neighbours: the streamed product of the solve passes
+  // (the factor pass keeps y in Y), else the RHS tiles
+  if (h->corr_ok && b.d <= kCorrMaxD)
+    e = launch_large_corr(h->corr_map_li, h->corr_map_w, b, l, kSubB, h->sms, h->stream);
+  else
+    e = launch_large_sub<float>(b, l, kSubBRhsOnly, 1,
+                                grid_for(h, large_sub_tasks(p, l, kSubBRhsOnly, 1, b.d, 4, 0, 0)), h->smem, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  return e;
+}
+
 // One factor and/or RHS pass over all levels, persistent or per level.
 // Large-block path: three tile sub-phases per level (see bdss_large.cu).
 template <typename T>
@@ -371,6 +396,11 @@ static cudaError_t run_levels_large(bdss_ctx *h, const Args<T> &a, bool factor, 
       if constexpr (sizeof(T) == 8) {
         if (emu_factor && sub == 2) {
           e = schur_emu_level(h, b, l);
+          continue;
+        }
+      } else {
+        if (tc_factor && sub == 2 && h->ts_ok) {
+          e = schur_tf32_level(h, b, l);
           continue;
         }
       }
@@ -555,6 +585,10 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
     ok = em == cudaSuccess && ws_alloc(h, (void **)&h->d_tmap, sizeof(CUtensorMap)) &&
          cudaMemcpy(h->d_tmap, &map, sizeof(CUtensorMap), cudaMemcpyHostToDevice) == cudaSuccess;
     h->tf32 = ok ? 1 : 0;
+    if (ok) {
+      h->ts_map_w = map;
+      h->ts_ok = 1;
+    }
   }
   if (ok && is_mixed(h)) {
     const size_t nd = (size_t)N * n * d_max;

@@ -590,6 +590,350 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// TF32 Schur products on the tensor cores, pipelined (the separator update of
+// Algorithm 3 in the TF32 mode of the tiled path).  An output tile of
+// 128 x 128 (D's lower part: one round per eliminated neighbour, accumulated;
+// E: one round) takes, per K chunk of 32, twelve tcgen05.mma (kind::tf32,
+// K = 8): hi*hi + hi*lo + lo*hi, the 3xTF32 product, into an FP32
+// accumulator in TMEM, where hi is W rounded to TF32 and lo = W - hi.
+// Roles (320 threads):
+//   warp 0     TMA: the raw W slabs of the A and B rows (2 x 16 KB per chunk)
+//              into a ring of two stages;
+//   warps 6-9  split each raw stage into hi and lo slabs (the swizzled
+//              layout is element-position preserving) in a second ring;
+//   warp 1     one thread issues the MMAs of a split stage and commits it;
+//   warps 2-5  drain the accumulator, two buffers, so that a tile's
+//              epilogue runs under the next tile's products.
+// Every wait is bounded; a timed-out wait aborts every role.
+// ---------------------------------------------------------------------------
+constexpr int kTsRaw = 2 * kTcSlab;     // raw A | B of one chunk
+constexpr int kTsSplit = 4 * kTcSlab;   // A hi | A lo | B hi | B lo
+constexpr int kTsStages = 2;            // stages of each ring
+constexpr int kTsThreads = 320;
+constexpr int kTsSplitters = 128;       // warps 6-9
+constexpr uint32_t kTsTmemCols = 2 * kTcN;
+constexpr size_t kTsSmem = (size_t)kTsStages * (kTsRaw + kTsSplit) + 1024;
+
+__device__ __forceinline__ bool ts_try(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait; gives up early when another role aborted (abort != null).
+__device__ __forceinline__ bool ts_wait(uint64_t *bar, uint32_t parity, long long timeout_ns, volatile int *abort) {
+  long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (ts_try(bar, parity)) return true;
+    if ((it & 63) == 63) {
+      if (abort && *abort) return false;
+      const long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > timeout_ns) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive_local(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct TsTile {
+  long long k;       // separator 2k
+  int isD, ti, tj, nr;
+  // rows (in the W buffer) of the A and B operands of rounds 0 and 1; scalar
+  // fields, so that the tile stays in registers
+  long long ra0, ra1, rb0, rb1;
+  __device__ long long a_of(int r) const { return r == 0 ? ra0 : ra1; }
+  __device__ long long b_of(int r) const { return r == 0 ? rb0 : rb1; }
+};
+
+__device__ __forceinline__ TsTile ts_tile(const Args<float> &a, int l, long long u) {
+  const int n = a.p.n, nt = (n + kTcM - 1) / kTcM, nD = nt * (nt + 1) / 2, per = nD + nt * nt;
+  const long long Nl = a.p.Nl[l], slot0 = a.p.off[l];
+  TsTile T;
+  T.k = u / per;
+  const int t = (int)(u - T.k * per);
+  const long long s = 2 * T.k;
+  T.nr = 0;
+  T.ra0 = T.ra1 = T.rb0 = T.rb1 = 0;
+  if (t < nD) {
+    T.isD = 1;
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    T.ti = ti;
+    T.tj = t - ti * (ti + 1) / 2;
+    const long long bm = (slot0 + s - 1) * n, bp = (slot0 + s) * n;
+    const bool hasM = s >= 2, hasP = s + 1 < Nl;
+    // round 0: the left neighbour if present, else the right one
+    T.ra0 = (hasM ? bm : bp) + T.ti * kTcM;
+    T.rb0 = (hasM ? bm : bp) + T.tj * kTcM;
+    T.ra1 = bp + T.ti * kTcM;
+    T.rb1 = bp + T.tj * kTcM;
+    T.nr = (int)hasM + (int)hasP;
+  } else {
+    T.isD = 0;
+    T.ti = (t - nD) / nt;
+    T.tj = (t - nD) - T.ti * nt;
+    if (s + 2 < Nl) {
+      T.ra0 = (slot0 + s + 1) * n + T.ti * kTcM;
+      T.rb0 = (slot0 + s) * n + T.tj * kTcM;
+      T.nr = 1;
+    }
+  }
+  return T;
+}
+
+__global__ void __launch_bounds__(kTsThreads, 1)
+    k_tf32_schur(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ Args<float> a, int l) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t tfull[kTsStages], tempty[kTsStages], sfull[kTsStages], sempty[kTsStages];
+  __shared__ uint64_t acc_full[2], acc_empty[2], drain;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort, s_go;
+  if (threadIdx.x == 0) s_go = ld_relaxed_i32(&a.st->status) == 0;
+  __syncthreads();
+  if (!s_go) return;
+  unsigned char *raw = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char *split = raw + (size_t)kTsStages * kTsRaw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.p.n, nt = (n + kTcM - 1) / kTcM, kchunks = (n + kTcK - 1) / kTcK;
+  const long long Nl = a.p.Nl[l];
+  const long long tiles = ((Nl + 1) / 2) * (long long)(nt * (nt + 1) / 2 + nt * nt);
+  volatile int *abort = &s_abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTsStages; ++s) {
+      mbar_init(&tfull[s], 1);
+      mbar_init(&tempty[s], kTsSplitters);
+      mbar_init(&sfull[s], kTsSplitters);
+      mbar_init(&sempty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(&drain, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(&s_tmem, kTsTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  auto fail = [&]() {
+    *abort = 1;
+    set_status(a.st, kStTimeout, l, -1);
+  };
+
+  if (warp == 0) {
+    // ---- TMA producer: raw slabs ------------------------------------------------
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      bool stop = false;
+      for (long long u = blockIdx.x; u < tiles && !stop; u += gridDim.x) {
+        const TsTile T = ts_tile(a, l, u);
+        for (int r = 0; r < T.nr && !stop; ++r)
+          for (int kc = 0; kc < kchunks; ++kc) {
+            if (!ts_wait(&tempty[st], ph ^ 1, a.timeout_ns, abort)) {
+              fail();
+              stop = true;
+              break;
+            }
+            unsigned char *base = raw + (size_t)st * kTsRaw;
+            mbar_expect_tx(&tfull[st], kTsRaw);
+            tma_load_2d(base, &mapW, kc * kTcK, (int)T.a_of(r), &tfull[st]);
+            tma_load_2d(base + kTcSlab, &mapW, kc * kTcK, (int)T.b_of(r), &tfull[st]);
+            if (++st == kTsStages) { st = 0; ph ^= 1; }
+          }
+      }
+      // wait out the loads still in flight (each stage's last armed phase)
+      for (int s = 0; s < kTsStages; ++s) ts_wait(&tfull[s], (s < st) ? ph : (ph ^ 1), a.timeout_ns, nullptr);
+    }
+  } else if (warp >= 6) {
+    // ---- split warps: raw -> hi | lo -------------------------------------------
+    const int sid = threadIdx.x - 6 * 32;
+    int ts = 0, ss = 0;
+    uint32_t tph = 0, sph = 0;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < tiles && !stop; u += gridDim.x) {
+      const TsTile T = ts_tile(a, l, u);
+      for (int r = 0; r < T.nr && !stop; ++r)
+        for (int kc = 0; kc < kchunks; ++kc) {
+          // warp-uniform waits: lane 0 polls, the others then observe the phase
+          int ok = 0;
+          if (lane == 0)
+            ok = (ts_wait(&tfull[ts], tph, a.timeout_ns, abort) && ts_wait(&sempty[ss], sph ^ 1, a.timeout_ns, abort))
+                     ? 1
+                     : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            if (lane == 0) fail();
+            stop = true;
+            break;
+          }
+          if (lane != 0) {
+            ts_try(&tfull[ts], tph);
+            ts_try(&sempty[ss], sph ^ 1);
+          }
+          const float4 *src = reinterpret_cast<const float4 *>(raw + (size_t)ts * kTsRaw);
+          unsigned char *dst = split + (size_t)ss * kTsSplit;
+#pragma unroll 4
+          for (int i = sid; i < kTsRaw / 16; i += kTsSplitters) {
+            const int which = i / (kTcSlab / 16), j = i - which * (kTcSlab / 16);  // A or B, float4 in slab
+            const float4 x = src[i];
+            float4 h, o;
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+            float hs[4], os[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              hs[q] = __uint_as_float((__float_as_uint(xs[q]) + 0x1000u) & 0xFFFFE000u);
+              os[q] = xs[q] - hs[q];
+            }
+            h = make_float4(hs[0], hs[1], hs[2], hs[3]);
+            o = make_float4(os[0], os[1], os[2], os[3]);
+            reinterpret_cast<float4 *>(dst + (size_t)which * 2 * kTcSlab)[j] = h;
+            reinterpret_cast<float4 *>(dst + (size_t)which * 2 * kTcSlab + kTcSlab)[j] = o;
+          }
+          fence_proxy_async_smem();  // the MMAs read the split slabs through the async proxy
+          mbar_arrive_local(&tempty[ts]);
+          mbar_arrive_local(&sfull[ss]);
+          if (++ts == kTsStages) { ts = 0; tph ^= 1; }
+          if (++ss == kTsStages) { ss = 0; sph ^= 1; }
+        }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ------------------------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc_tf32(kTcM, kTcN);
+      int st = 0;
+      uint32_t ph = 0;
+      long long i = 0;  // tiles with work so far: accumulator buffer i & 1
+      bool stop = false;
+      for (long long u = blockIdx.x; u < tiles && !stop; u += gridDim.x) {
+        const TsTile T = ts_tile(a, l, u);
+        if (T.nr == 0) continue;
+        const int b = (int)(i & 1);
+        if (!ts_wait(&acc_empty[b], (uint32_t)((i >> 1) & 1), a.timeout_ns, abort)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * kTcN);
+        bool first = true;
+        for (int r = 0; r < T.nr && !stop; ++r)
+          for (int kc = 0; kc < kchunks; ++kc) {
+            if (!ts_wait(&sfull[st], ph, a.timeout_ns, abort)) {
+              fail();
+              stop = true;
+              break;
+            }
+            tc_fence_after();
+            const unsigned char *base = split + (size_t)st * kTsSplit;
+            const unsigned char *Ahi = base, *Alo = base + kTcSlab, *Bhi = base + 2 * kTcSlab,
+                                *Blo = base + 3 * kTcSlab;
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 8; ++kk) {
+              const int off = kk * 32;  // 8 TF32 = 32 bytes along K inside the swizzle atom
+              tc_mma_tf32(d, tc_desc_sw128(Ahi, off), tc_desc_sw128(Bhi, off), idesc, first ? 0u : 1u);
+              first = false;
+              tc_mma_tf32(d, tc_desc_sw128(Ahi, off), tc_desc_sw128(Blo, off), idesc, 1u);
+              tc_mma_tf32(d, tc_desc_sw128(Alo, off), tc_desc_sw128(Bhi, off), idesc, 1u);
+            }
+            tc_commit(&sempty[st]);
+            if (++st == kTsStages) { st = 0; ph ^= 1; }
+          }
+        if (stop) break;
+        tc_commit(&acc_full[b]);
+        ++i;
+      }
+      // every MMA issued has completed before TMEM is released
+      tc_commit(&drain);
+      ts_wait(&drain, 0, a.timeout_ns, nullptr);
+    }
+  } else {
+    // ---- epilogue: warps 2..5, TMEM lane quarter warp % 4 ---------------------
+    const int quarter = warp & 3;
+    const size_t nn = (size_t)n * n;
+    tc_fence_before();
+    mbar_arrive_local(&acc_empty[0]);
+    mbar_arrive_local(&acc_empty[1]);
+    long long i = 0;
+    for (long long u = blockIdx.x; u < tiles; u += gridDim.x) {
+      const TsTile T = ts_tile(a, l, u);
+      if (T.nr == 0) continue;
+      const int b = (int)(i & 1);
+      int ok = 0;
+      if (lane == 0) ok = ts_wait(&acc_full[b], (uint32_t)((i >> 1) & 1), a.timeout_ns, abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
+      if (lane != 0) ts_try(&acc_full[b], (uint32_t)((i >> 1) & 1));
+      tc_fence_after();
+      const int R = T.ti * kTcM + 32 * quarter + lane;
+      const long long s = 2 * T.k, orig = s << l;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * kTcN);
+#pragma unroll 1
+      for (int cb = 0; cb < kTcN / 32; ++cb) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(cb * 32), v);
+        if (R >= n) continue;
+        const int C0 = T.tj * kTcN + cb * 32;
+        if (T.isD) {
+          if (C0 > R) continue;  // the block lies above the diagonal for this row
+          float *Dg = a.Ld + (size_t)orig * nn + (size_t)R * n;
+          float base[32];
+          // every load of the block first (independent, in flight together),
+          // then the stores
+          if (l == 0) {
+            const double *Ag = a.A_diag + (size_t)orig * nn;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int C = C0 + j;
+              const bool in = C <= R && C < n;
+              const double x = in ? ldcg(Ag + (size_t)R * n + C) : 0.0;
+              const double y = in ? ldcg(Ag + (size_t)C * n + R) : 0.0;
+              base[j] = 0.5f * ((float)x + (float)y);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int C = C0 + j;
+              base[j] = (C <= R && C < n) ? ldcg(Dg + C) : 0.0f;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int C = C0 + j;
+            if (C <= R && C < n) Dg[C] = base[j] - v[j];
+          }
+        } else {
+          float *Eg = a.Eb + ((size_t)a.p.off[l + 1] + (size_t)T.k) * nn + (size_t)R * n;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int C = C0 + j;
+            if (C < n) Eg[C] = -v[j];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive_local(&acc_empty[b]);
+      ++i;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kTsTmemCols);
+}
+
 // FP64 residual for large blocks: one CTA per block row, one thread per row r
 // of the block with up to 16 right-hand-side columns in registers:
 //   R[r][c] = B[r][c] - 0.5 sum_p (A[r][p] + A[p][r]) x_i[p][c]
@@ -691,7 +1035,7 @@ cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm, int 
                            (const void *)k_large_persistent<float, true>, (const void *)k_large_sub<float, true>,
                            (const void *)k_large_top<T>, (const void *)k_residual_rows,
                            (const void *)k_tc_selftest, (const void *)k_large_corr<1>,
-                           (const void *)k_large_corr<2>};
+                           (const void *)k_large_corr<2>, (const void *)k_tf32_schur};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -765,6 +1109,15 @@ cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW,
   else
     k_large_corr<2><<<grid, 2 * kThreads, corr_smem_bytes(a.p.n, kCorrStages, 2), s>>>(mapLi, mapW, a, l, sub,
                                                                                       kCorrStages);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tf32_schur(const CUtensorMap &mapW, const Args<float> &a, int l, int sms, cudaStream_t s) {
+  const int n = a.p.n, nt = (n + kTcM - 1) / kTcM;
+  const long long tiles = ((a.p.Nl[l] + 1) / 2) * (long long)(nt * (nt + 1) / 2 + nt * nt);
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  k_tf32_schur<<<grid, kTsThreads, kTsSmem, s>>>(mapW, a, l);
   return cudaGetLastError();
 }
 

@@ -480,9 +480,11 @@ __device__ void largeA2(const Args<T> &a, int l, long long j, int v, bool factor
   for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
     const int cc = e / n, i = e - cc * n, c = c0 + cc;
     const T val = sV[(size_t)cc * lv + i];
-    if (c < nW && c < n) W[(size_t)(j - 1) * nn + (size_t)c * n + i] = val;
-    else if (c < nW) { if (hasR) W[(size_t)j * nn + (size_t)(c - n) * n + i] = val; }
+    long long wo = -1;  // element of the coupling buffer, if this is a coupling slot
+    if (c < nW && c < n) wo = (long long)((size_t)(j - 1) * nn + (size_t)c * n + i);
+    else if (c < nW) { if (hasR) wo = (long long)((size_t)j * nn + (size_t)(c - n) * n + i); }
     else if (c >= nW + nI) a.Y[(size_t)orig * n * d + (size_t)i * d + (c - nW - nI)] = val;
+    if (wo >= 0) W[wo] = val;
   }
   if (nI) {
     // columns u0..u1-1 of L^{-1}, row-major in Li: consecutive threads take

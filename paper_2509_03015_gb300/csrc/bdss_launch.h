@@ -56,6 +56,10 @@ cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, in
 cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW, const Args<float> &a, int l,
                               int sub, int sms, cudaStream_t s);
 
+// TF32 Schur products of level l on the tensor cores (pipelined, warp roles):
+// a map over Wb (boxes of 128 rows x 32 columns).
+cudaError_t launch_tf32_schur(const CUtensorMap &mapW, const Args<float> &a, int l, int sms, cudaStream_t s);
+
 // Sub-phase code of the large path: the separators' RHS tiles alone (their D
 // and E tiles ran elsewhere, e.g. on the tensor cores).
 constexpr int kSubBRhsOnly = 4;
