@@ -83,7 +83,8 @@ struct bdss_ctx {
   int schur_emu_ready = 0;
   int schur_emu_on = 0;
   // large mixed path: streamed solve passes (maps over Li and Wb)
-  CUtensorMap corr_map_li, corr_map_w;
+  CorrMaps corr_maps[3];  // split factors P = 1, 2, 4
+  int corr_max_split = 1;
   int corr_ok = 0;
   // TF32 mode: the pipelined 3xTF32 Schur tiles read W through this map
   CUtensorMap ts_map_w;
@@ -312,7 +313,7 @@ static cudaError_t run_corr_passes(bdss_ctx *h, const Args<float> &b) {
   for (int l = 0; l < p.L && e == cudaSuccess; ++l)
     for (int sub = kSubA2; sub <= kSubB && e == cudaSuccess; ++sub) {
       kt_begin(h, h->kt_cls);
-      e = launch_large_corr(h->corr_map_li, h->corr_map_w, b, l, sub, h->sms, h->stream);
+      e = launch_large_corr(h->corr_maps, h->corr_max_split, b, l, sub, h->sms, h->stream);
       kt_end(h, 1);
       h->launches += 1;
     }
@@ -322,7 +323,14 @@ static cudaError_t run_corr_passes(bdss_ctx *h, const Args<float> &b) {
   h->launches += 1;
   for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
     kt_begin(h, h->kt_cls);
-    e = launch_large_corr(h->corr_map_li, h->corr_map_w, b, l, kSubC, h->sms, h->stream);
+    if (corr_split(p.n, p.Nl[l] / 2, h->sms, h->corr_max_split) > 1) {
+      // few blocks: t = y - W x, then x = L^{-T} t, each block split over SMs
+      e = launch_large_corr(h->corr_maps, h->corr_max_split, b, l, kSubC1, h->sms, h->stream);
+      if (e == cudaSuccess) e = launch_large_corr(h->corr_maps, h->corr_max_split, b, l, kSubC2, h->sms, h->stream);
+      h->launches += 1;
+    } else {
+      e = launch_large_corr(h->corr_maps, h->corr_max_split, b, l, kSubC, h->sms, h->stream);
+    }
     kt_end(h, 1);
     h->launches += 1;
   }
@@ -342,7 +350,7 @@ static cudaError_t schur_tf32_level(bdss_ctx *h, const Args<float> &b, int l) {
   // b_s -= W^T y of the neighbours: the streamed product of the solve passes
   // (the factor pass keeps y in Y), else the RHS tiles
   if (h->corr_ok && b.d <= kCorrMaxD)
-    e = launch_large_corr(h->corr_map_li, h->corr_map_w, b, l, kSubB, h->sms, h->stream);
+    e = launch_large_corr(h->corr_maps, h->corr_max_split, b, l, kSubB, h->sms, h->stream);
   else
     e = launch_large_sub<float>(b, l, kSubBRhsOnly, 1,
                                 grid_for(h, large_sub_tasks(p, l, kSubBRhsOnly, 1, b.d, 4, 0, 0)), h->smem, h->stream);
@@ -599,8 +607,25 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
       ok = ok && ws_alloc(h, (void **)&h->Yt, nd * sizeof(float));
       ok = ok && ws_alloc(h, (void **)&h->Ltinv, 2 * nn * sizeof(float));
       if (ok && n % 4 == 0 && d_max <= 16 && corr_smem_bytes(n) <= (size_t)smem_optin) {
-        h->corr_ok = make_f32_map(&h->corr_map_li, (const float *)h->Li, N * n, n, n) == cudaSuccess &&
-                     make_f32_map(&h->corr_map_w, (const float *)h->Wb, (long long)slots * n, n, n) == cudaSuccess;
+        const float *Lif = (const float *)h->Li, *Wbf = (const float *)h->Wb;
+        const long long rl = N * n, rw = (long long)slots * n;
+        CorrMaps &m0 = h->corr_maps[0];
+        h->corr_ok = make_f32_map(&m0.rowsLi, Lif, rl, n, n) == cudaSuccess &&
+                     make_f32_map(&m0.rowsW, Wbf, rw, n, n) == cudaSuccess;
+        m0.colsLi = m0.rowsLi;  // P = 1: the column products use bulk copies
+        m0.colsW = m0.rowsW;
+        if (h->corr_ok && n % 32 == 0) {
+          bool split = true;
+          for (int i = 1; i <= 2 && split; ++i) {
+            const int R = n >> i;
+            CorrMaps &m = h->corr_maps[i];
+            split = make_f32_map_box(&m.rowsLi, Lif, rl, n, 32, R, true) == cudaSuccess &&
+                    make_f32_map_box(&m.rowsW, Wbf, rw, n, 32, R, true) == cudaSuccess &&
+                    make_f32_map_box(&m.colsLi, Lif, rl, n, R, 32, false) == cudaSuccess &&
+                    make_f32_map_box(&m.colsW, Wbf, rw, n, R, 32, false) == cudaSuccess;
+            if (split) h->corr_max_split = 1 << i;
+          }
+        }
       }
     }
     if (ok && h->large && d_max <= kEmuDp) {  // the tensor-core FP64 residual

@@ -181,11 +181,16 @@ __host__ __device__ inline int corr_pad(int n) { return (n + kCorrKR - 1) / kCor
 __host__ __device__ inline size_t corr_stage_bytes(int n) { return (size_t)kCorrKR * n * sizeof(float); }
 // stage stride: a multiple of 1024 bytes, the period of the 128-byte swizzle
 __host__ __device__ inline size_t corr_stage_stride(int n) { return (corr_stage_bytes(n) + 1023) & ~(size_t)1023; }
-size_t corr_smem_bytes(int n, int stages, int q) {
-  return stages * corr_stage_stride(n) + (size_t)2 * corr_pad(n) * kRowCols * sizeof(float) +
+// Shared memory of a streamed pass: `stages` chunks of 32 x n/P floats, two
+// operand blocks and the partial sums of q threads per row.
+size_t corr_smem_bytes(int n, int stages, int q, int P) {
+  return stages * corr_stage_stride(n / P) + (size_t)2 * corr_pad(n) * kRowCols * sizeof(float) +
          (size_t)(q - 1) * kThreads * kRowCols * sizeof(float) + 1024;
 }
-size_t corr_smem_bytes(int n) { return corr_smem_bytes(n, kCorrStages, 2); }
+size_t corr_smem_bytes(int n) {
+  const size_t a = corr_smem_bytes(n, kCorrStages, 2, 1), b = corr_smem_bytes(n, kCorrStages, 4, 4);
+  return a > b ? a : b;
+}
 
 struct CorrProd {
   long long row0;  // first row of the block in its buffer (block index x n)
@@ -210,9 +215,13 @@ __device__ __forceinline__ int corr_prods(const Args<float> &a, int l, int sub, 
   }
   const long long j = 2 * t + 1;
   int c = 0;
+  if (sub == kSubC2) {
+    P[0] = {(j << l) * n, 1, 1};
+    return 1;
+  }
   P[c++] = {(off + j - 1) * n, 1, 0};
   if (j + 1 < Nl) P[c++] = {(off + j) * n, 1, 0};
-  P[c++] = {(j << l) * n, 1, 1};
+  if (sub == kSubC) P[c++] = {(j << l) * n, 1, 1};
   return c;
 }
 
@@ -250,11 +259,11 @@ __device__ __forceinline__ void corr_rows_chunk(const unsigned char *stage, int 
 }
 
 // acc[c] += sum over the rows kk0 .. kk1 - 1 (k0 + kk) of column r of a row chunk.
-__device__ __forceinline__ void corr_cols_chunk(const float *stage, int n, int r, int k0, int kk0, int kk1,
+__device__ __forceinline__ void corr_cols_chunk(const float *stage, int pitch, int r, int k0, int kk0, int kk1,
                                                 const float *V, float (&acc)[kRowCols]) {
 #pragma unroll 4
   for (int kk = kk0; kk < kk1; ++kk) {
-    const float p = stage[(size_t)kk * n + r];
+    const float p = stage[(size_t)kk * pitch + r];
     const float4 *v4 = reinterpret_cast<const float4 *>(V + (size_t)(k0 + kk) * kRowCols);
 #pragma unroll
     for (int c4 = 0; c4 < kRowCols / 4; ++c4) {
@@ -307,9 +316,9 @@ __device__ __forceinline__ void corr_reduce(float (&acc)[kRowCols], float *red, 
 }
 
 template <int kQ>
-__global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
-    k_large_corr(const __grid_constant__ CUtensorMap mapLi, const __grid_constant__ CUtensorMap mapW,
-                 const __grid_constant__ Args<float> a, int l, int sub, int stages) {
+__global__ void __launch_bounds__(kQ == 2 ? 2 * kThreads : kThreads, kQ == 1 ? 2 : 1)
+    k_large_corr(const __grid_constant__ CorrMaps maps, const __grid_constant__ Args<float> a, int l, int sub,
+                 int stages, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t full[kCorrStages], vbar;
   __shared__ int s_ok;
@@ -318,12 +327,15 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
   __syncthreads();
   if (!s_ok) return;
   const int n = a.p.n, d = a.d, np = corr_pad(n);
-  // thread = (row or column r of the block, share kq of every chunk)
-  const int r = threadIdx.x % kThreads, kq = threadIdx.x / kThreads;
-  const bool active = r < n;
+  // work item = (block, part h of P); thread = (row or column r of the part,
+  // share kq of every chunk); g = h R + r indexes the block's data
+  const int RT = blockDim.x / kQ, R = n / P;
+  const int r = threadIdx.x % RT, kq = threadIdx.x / RT;
+  const bool active = r < R;
+  const bool cols = (sub == kSubC || sub == kSubC1 || sub == kSubC2);
   const long long Nl = a.p.Nl[l];
-  const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2;
-  const size_t SB = corr_stage_bytes(n), SS = corr_stage_stride(n), nd = (size_t)n * d;
+  const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2, items = tasks * P;
+  const size_t SB = corr_stage_bytes(R), SS = corr_stage_stride(R), nd = (size_t)n * d;
   const int nch = (n + kCorrKR - 1) / kCorrKR;
   // 1024-byte aligned ring, by pointer arithmetic on the shared array so that
   // the compiler keeps shared-memory loads (an integer round trip would make
@@ -339,28 +351,36 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
   }
   __syncthreads();
 
-  // producer cursor (thread 0): task pt, product pp, chunk pc
+  // producer cursor (thread 0): work item pt, product pp, chunk pc
   long long pt = blockIdx.x;
   int pp = 0, pc = 0, pn = 0;
   CorrProd PP[3];
   long long issued = 0;
   auto issue = [&](int stage) {
-    while (pt < tasks && pp >= pn) {
+    while (pt < items && pp >= pn) {
       pt += gridDim.x;
       pp = 0;
       pc = 0;
-      pn = pt < tasks ? corr_prods(a, l, sub, pt, PP) : 0;
+      pn = pt < items ? corr_prods(a, l, sub, pt / P, PP) : 0;
     }
-    if (pt >= tasks) return;
-    const CorrProd &P = PP[pp];
+    if (pt >= items) return;
+    const CorrProd &Q = PP[pp];
+    const int h = (int)(pt % P);
     unsigned char *dst = ring + (size_t)stage * SS;
-    if (!P.trans) {
+    if (!Q.trans) {
+      // rows h R .. h R + R - 1 of the block, columns pc*32 .. +31
       mbar_expect_tx(&full[stage], (uint32_t)SB);
-      tma_load_2d(dst, P.inLi ? &mapLi : &mapW, pc * kCorrKR, (int)P.row0, &full[stage]);
+      tma_load_2d(dst, Q.inLi ? &maps.rowsLi : &maps.rowsW, pc * kCorrKR, (int)(Q.row0 + (long long)h * R),
+                  &full[stage]);
+    } else if (P > 1) {
+      // rows pc*32 .. +31 of the block, columns h R .. h R + R - 1
+      mbar_expect_tx(&full[stage], (uint32_t)SB);
+      tma_load_2d(dst, Q.inLi ? &maps.colsLi : &maps.colsW, h * R, (int)(Q.row0 + (long long)pc * kCorrKR),
+                  &full[stage]);
     } else {
       const int rows = min(kCorrKR, n - pc * kCorrKR);
       const uint32_t bytes = (uint32_t)((size_t)rows * n * sizeof(float));
-      const float *src = (P.inLi ? a.Li : a.Wb) + (size_t)(P.row0 + (long long)pc * kCorrKR) * n;
+      const float *src = (Q.inLi ? a.Li : a.Wb) + (size_t)(Q.row0 + (long long)pc * kCorrKR) * n;
       mbar_expect_tx(&full[stage], bytes);
       bulk_load(dst, src, bytes, &full[stage]);
     }
@@ -371,7 +391,7 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
     }
   };
   if (threadIdx.x == 0) {
-    pn = pt < tasks ? corr_prods(a, l, sub, pt, PP) : 0;
+    pn = pt < items ? corr_prods(a, l, sub, pt / P, PP) : 0;
     for (int s = 0; s < stages; ++s) issue(s);
   }
   bool vpend = false;  // an operand copy may still be in flight (timeout path)
@@ -385,7 +405,9 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
   // with 16 columns an operand block is n x 16 contiguous floats: one bulk copy
   const bool bulkV = (d == kRowCols);
   const uint32_t vbytes = (uint32_t)((size_t)n * kRowCols * sizeof(float));
-  for (long long t = blockIdx.x; t < tasks && ok; t += gridDim.x) {
+  for (long long u = blockIdx.x; u < items && ok; u += gridDim.x) {
+    const long long t = u / P;
+    const int g = (int)(u % P) * R + r;  // row / column of the block this thread serves
     long long orig;
     bool hasM = false;
     int npr;
@@ -405,6 +427,11 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
       if (hasM) src0 = ys + (size_t)((s - 1) << l) * nd;
       if (hasP) src1 = ys + (size_t)((s + 1) << l) * nd;
       npr = (int)hasM + (int)hasP;
+    } else if (sub == kSubC2) {
+      const long long j = 2 * t + 1;
+      orig = j << l;
+      src0 = ys + (size_t)orig * nd;  // t, formed by C1 in place of y_j
+      npr = 1;
     } else {
       const long long j = 2 * t + 1;
       orig = j << l;
@@ -412,8 +439,8 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
       src0 = a.Y + (size_t)((j - 1) << l) * nd;
       if (hasR) src1 = a.Y + (size_t)((j + 1) << l) * nd;
       yj = ys + (size_t)orig * nd;  // y_j: read at the t step, fetched into L2 now
-      if (active && kq == 0) prefetch_l2(yj + (size_t)r * d, (size_t)d * sizeof(float));
-      npr = hasR ? 3 : 2;
+      if (active && kq == 0) prefetch_l2(yj + (size_t)g * d, (size_t)d * sizeof(float));
+      npr = (sub == kSubC1) ? (hasR ? 2 : 1) : (hasR ? 3 : 2);
     }
     const uint32_t nsrc = (src0 ? 1u : 0u) + (src1 ? 1u : 0u);
     if (bulkV && !src0d) {
@@ -448,7 +475,7 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
         // products are done (the last chunk ended with a barrier)
         corr_reduce<kQ>(acc, red, r, kq);
         if (active && kq == 0) {
-          const float *yr = yj + (size_t)r * d;
+          const float *yr = yj + (size_t)g * d;
           if (d == kRowCols) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -467,10 +494,10 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
         for (int c = 0; c < kRowCols; ++c) acc[c] = 0.0f;
         __syncthreads();
       }
-      const float *V = (sub == kSubA2)   ? sV0
-                       : (sub == kSubB) ? ((p == 0 && hasM) ? sV0 : sV1)
-                       : (lastC || p == 0) ? sV0
-                                           : sV1;
+      const float *V = (sub == kSubA2 || sub == kSubC2) ? sV0
+                       : (sub == kSubB)                  ? ((p == 0 && hasM) ? sV0 : sV1)
+                       : (lastC || p == 0)               ? sV0
+                                                         : sV1;
       for (int c = 0; c < nch; ++c) {
         if (!mbar_wait_cta(&full[cs], cph, a.timeout_ns, &s_ok)) {
           if (threadIdx.x == 0) set_status(a.st, kStTimeout, l, -1);
@@ -479,9 +506,9 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
         }
         const unsigned char *stage = ring + (size_t)cs * SS;
         if (active) {
-          if (sub == kSubC) {
+          if (cols) {
             const int rows = min(kCorrKR, n - c * kCorrKR), per = kCorrKR / kQ;
-            corr_cols_chunk(reinterpret_cast<const float *>(stage), n, r, c * kCorrKR, kq * per,
+            corr_cols_chunk(reinterpret_cast<const float *>(stage), P > 1 ? R : n, r, c * kCorrKR, kq * per,
                             min(rows, (kq + 1) * per), V, acc);
           } else {
             corr_rows_chunk<8 / kQ>(stage, r, c * kCorrKR, kq * (8 / kQ), V, acc);
@@ -502,7 +529,7 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
     if (!ok) continue;
     corr_reduce<kQ>(acc, red, r, kq);
     if (!active || kq != 0) continue;
-    const size_t o = (size_t)orig * nd + (size_t)r * d;
+    const size_t o = (size_t)orig * nd + (size_t)g * d;
     if (d == kRowCols) {
       // a thread's row of the block is 16 contiguous values
       if (sub == kSubA2) {
@@ -534,6 +561,14 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
         for (int q = 0; q < 4; ++q)
           dst[q] = make_float4(base[4 * q] - acc[4 * q], base[4 * q + 1] - acc[4 * q + 1],
                                base[4 * q + 2] - acc[4 * q + 2], base[4 * q + 3] - acc[4 * q + 3]);
+      } else if (sub == kSubC1) {
+        // t = y_j - (W_L x_{j-1} + W_R x_{j+1}), in place of y_j
+        float4 *yt = reinterpret_cast<float4 *>(const_cast<float *>(ys) + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 y4 = __ldcg(yt + q);
+          yt[q] = make_float4(y4.x - acc[4 * q], y4.y - acc[4 * q + 1], y4.z - acc[4 * q + 2], y4.w - acc[4 * q + 3]);
+        }
       } else {
         float4 *dst = reinterpret_cast<float4 *>(a.Y + o);
 #pragma unroll
@@ -556,6 +591,11 @@ __global__ void __launch_bounds__(kThreads * kQ, kQ == 1 ? 2 : 1)
 #pragma unroll
       for (int c = 0; c < kRowCols; ++c)
         if (c < d) a.Yt[o + c] = acc[c];
+    } else if (sub == kSubC1) {
+      float *yt = const_cast<float *>(ys) + o;
+#pragma unroll
+      for (int c = 0; c < kRowCols; ++c)
+        if (c < d) yt[c] = ldcg(yt + c) - acc[c];
     } else if (sub == kSubB) {
 #pragma unroll
       for (int c = 0; c < kRowCols; ++c)
@@ -1035,7 +1075,8 @@ cudaError_t configure_large(int n, int d, size_t *smem, int *blocks_per_sm, int 
                            (const void *)k_large_persistent<float, true>, (const void *)k_large_sub<float, true>,
                            (const void *)k_large_top<T>, (const void *)k_residual_rows,
                            (const void *)k_tc_selftest, (const void *)k_large_corr<1>,
-                           (const void *)k_large_corr<2>, (const void *)k_tf32_schur};
+                           (const void *)k_large_corr<2>, (const void *)k_large_corr<4>,
+                           (const void *)k_tf32_schur};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -1091,24 +1132,47 @@ cudaError_t launch_large_top(const Args<T> &a, int factor, size_t smem, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW, const Args<float> &a, int l,
-                              int sub, int sms, cudaStream_t s) {
+// Split factor of a level's streamed pass: with few blocks each block's
+// output rows (or columns) are shared by P CTAs on different SMs (n a
+// multiple of 32, so that every chunk stays inside its block).
+int corr_split(int n, long long tasks, int sms, int max_split) {
+  if (n % 32 != 0) return 1;
+  if (max_split >= 4 && tasks * 4 <= sms) return 4;
+  if (max_split >= 2 && tasks * 2 <= sms) return 2;
+  return 1;
+}
+
+cudaError_t launch_large_corr(const CorrMaps *maps, int max_split, const Args<float> &a, int l, int sub, int sms,
+                              cudaStream_t s) {
+  const int n = a.p.n;
   const long long Nl = a.p.Nl[l];
   const long long tasks = (sub == kSubB) ? (Nl + 1) / 2 : Nl / 2;
   if (tasks <= 0) return cudaSuccess;
+  const int P = corr_split(n, tasks, sms, max_split);
+  if (P == 1 && (sub == kSubC1 || sub == kSubC2)) return cudaErrorInvalidValue;  // the fused C serves P = 1
+  if (P > 1) {
+    const long long items = tasks * P;
+    const int grid = (int)(items < sms ? items : sms);
+    const CorrMaps &m = maps[P == 2 ? 1 : 2];
+    if (P == 2)
+      k_large_corr<2><<<grid, kThreads, corr_smem_bytes(n, kCorrStages, 2, 2), s>>>(m, a, l, sub, kCorrStages, 2);
+    else
+      k_large_corr<4><<<grid, kThreads, corr_smem_bytes(n, kCorrStages, 4, 4), s>>>(m, a, l, sub, kCorrStages, 4);
+    return cudaGetLastError();
+  }
   // many blocks: two CTAs per SM with a two-stage ring each (more warps to
-  // hide latency, the same bytes in flight); few blocks: one CTA per block
-  // with a deeper ring
+  // hide latency, the same bytes in flight);
   //   few blocks: one CTA per block, two threads per row, a deeper ring
-  const bool pair = tasks >= 2LL * sms && 2 * (corr_smem_bytes(a.p.n, kCorrStagesPair, 1) + 1024) <= kCorrSmemPerSM;
+  const bool pair =
+      tasks >= 2LL * sms && 2 * (corr_smem_bytes(n, kCorrStagesPair, 1, 1) + 1024) <= kCorrSmemPerSM;
   const long long cap = pair ? 2LL * sms : (long long)sms;
   const int grid = (int)(tasks < cap ? tasks : cap);
   if (pair)
-    k_large_corr<1><<<grid, kThreads, corr_smem_bytes(a.p.n, kCorrStagesPair, 1), s>>>(mapLi, mapW, a, l, sub,
-                                                                                      kCorrStagesPair);
+    k_large_corr<1><<<grid, kThreads, corr_smem_bytes(n, kCorrStagesPair, 1, 1), s>>>(maps[0], a, l, sub,
+                                                                                   kCorrStagesPair, 1);
   else
-    k_large_corr<2><<<grid, 2 * kThreads, corr_smem_bytes(a.p.n, kCorrStages, 2), s>>>(mapLi, mapW, a, l, sub,
-                                                                                      kCorrStages);
+    k_large_corr<2><<<grid, 2 * kThreads, corr_smem_bytes(n, kCorrStages, 2, 1), s>>>(maps[0], a, l, sub,
+                                                                                   kCorrStages, 1);
   return cudaGetLastError();
 }
 
@@ -1148,7 +1212,16 @@ cudaError_t make_w_tensor_map(CUtensorMap *out, const float *Wb, long long rows,
 
 // 2-D map over `rows` rows of n floats: boxes of 32 columns x box_rows rows,
 // 128-byte swizzle.
+cudaError_t make_f32_map_box(CUtensorMap *out, const float *base, long long rows, int n, int box_cols,
+                             int box_rows, bool swizzle);
 cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, int n, int box_rows) {
+  return make_f32_map_box(out, base, rows, n, kTcK, box_rows, true);
+}
+
+// General form: boxes of box_cols x box_rows; the 128-byte swizzle needs
+// box_cols = 32.
+cudaError_t make_f32_map_box(CUtensorMap *out, const float *base, long long rows, int n, int box_cols,
+                             int box_rows, bool swizzle) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -1160,11 +1233,11 @@ cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, in
   }
   const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

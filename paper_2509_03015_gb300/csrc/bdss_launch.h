@@ -53,8 +53,22 @@ constexpr int kSubA1 = 0, kSubA2 = 1, kSubB = 2, kSubC = 3;
 constexpr int kCorrMaxD = 16;  // right-hand-side columns of one streamed pass
 size_t corr_smem_bytes(int n);
 cudaError_t make_f32_map(CUtensorMap *out, const float *base, long long rows, int n, int box_rows);
-cudaError_t launch_large_corr(const CUtensorMap &mapLi, const CUtensorMap &mapW, const Args<float> &a, int l,
-                              int sub, int sms, cudaStream_t s);
+cudaError_t make_f32_map_box(CUtensorMap *out, const float *base, long long rows, int n, int box_cols,
+                             int box_rows, bool swizzle);
+// The maps of one split factor P of the streamed passes: boxes of 32 columns x
+// n/P rows (row products, swizzled) and n/P columns x 32 rows (column
+// products) over Li and Wb.
+struct CorrMaps {
+  CUtensorMap rowsLi, rowsW, colsLi, colsW;
+};
+// maps[0]: P = 1 (rows maps over Li and Wb with boxes of n rows), maps[1]:
+// P = 2, maps[2]: P = 4; max_split bounds P (the maps that exist).
+int corr_split(int n, long long tasks, int sms, int max_split);
+cudaError_t launch_large_corr(const CorrMaps *maps, int max_split, const Args<float> &a, int l, int sub, int sms,
+                              cudaStream_t s);
+// Sub-phases of the split downward pass (levels of few blocks): C1 forms
+// t = y_j - W x of the neighbours in place in Yt, C2 x_j = L_j^{-T} t.
+constexpr int kSubC1 = 5, kSubC2 = 6;
 
 // TF32 Schur products of level l on the tensor cores (pipelined, warp roles):
 // a map over Wb (boxes of 128 rows x 32 columns).
