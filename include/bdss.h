@@ -132,15 +132,17 @@ typedef enum {
                                    (unless BDSS_OPT_REFINE_KRYLOV = 0); the copy of A_diag
                                    (N n^2 doubles) is allocated on first use.
                                    0 = return BDSS_ERR_NOT_SPD */
-  BDSS_OPT_SCHUR_EMU = 13,      /* FP64, 64 < n <= 256: 1 (default) = the Schur products of
-                                   the factorisation (the separator update of Algorithm 3,
+  BDSS_OPT_SCHUR_EMU = 13,      /* FP64, N > 1, 32 <= n <= 256: 1 = the Schur products of the
+                                   factorisation (the separator update of Algorithm 3,
                                    D - W^T W and -W^T W of Eq. 5's reduced system) on the
                                    tensor cores: each W row cut into ten BF16 digits below
                                    its maximum (59 bits), every digit product summed
                                    exactly in FP32, the rounds combined in FP64; one
                                    launch per level and phase even in persistent mode.
-                                   0 = on the FP64 ALU.  Setting 1 on a handle without it
-                                   gives BDSS_ERR_UNSUPPORTED */
+                                   0 = on the FP64 ALU (for n <= 64 the single persistent
+                                   launch).  Default 1 for 64 < n <= 256, 0 for n <= 64.
+                                   Setting 1 on a handle without it gives
+                                   BDSS_ERR_UNSUPPORTED */
   BDSS_OPT_RESIDUAL_EMU = 10,   /* mixed precision, 64 < n <= 256 and d_max <= 16: 1 (default)
                                    = the FP64 residual of the refinement on the tensor cores
                                    (BF16 digit slices, exact FP32 accumulation: see

@@ -290,17 +290,57 @@ static cudaError_t schur_emu_level(bdss_ctx *h, const Args<double> &b, int l) {
   kt_end(h, 1);
   h->launches += 1;
   if (e != cudaSuccess) return e;
+  // the next level's couplings: Eb on the tiled path, region l + 1 of Wb for n <= 64
+  double *En = (h->large ? b.Eb : b.Wb) + (size_t)p.off[l + 1] * nn;
   kt_begin(h, BDSS_KT_SCHUR_TC);
-  e = launch_emu_schur(Nl, p.n, l, h->Wslc, h->Wexp, b.A_diag, b.Ld, b.Eb + (size_t)p.off[l + 1] * nn, h->dst,
-                       h->timeout_ns, h->sms, h->stream);
+  e = launch_emu_schur(Nl, p.n, l, h->Wslc, h->Wexp, b.A_diag, b.Ld, En, h->dst, h->timeout_ns, h->sms, h->stream);
   kt_end(h, 1);
   h->launches += 1;
   if (e != cudaSuccess || b.d == 0) return e;
   kt_begin(h, h->kt_cls);
-  e = launch_large_sub<double>(b, l, kSubBRhsOnly, 1, grid_for(h, large_sub_tasks(p, l, kSubBRhsOnly, 1, b.d, 8, 0, 0)),
-                               h->smem, h->stream);
+  if (h->large) {
+    e = launch_large_sub<double>(b, l, kSubBRhsOnly, 1,
+                                 grid_for(h, large_sub_tasks(p, l, kSubBRhsOnly, 1, b.d, 8, 0, 0)), h->smem,
+                                 h->stream);
+  } else {  // phase B without the factor work is the separators' RHS update
+    const int cap = h->bps * h->sms;
+    e = launch_phaseB<double>(b, l, 0, grid_for(h, ((Nl + 1) / 2) * parts_B<double>(p, l, false, cap)), h->smem,
+                              h->stream);
+  }
   kt_end(h, 1);
   h->launches += 1;
+  return e;
+}
+
+// FP64 factorisation for n <= 64 with the Schur products on the tensor
+// cores: per level phase A (Cholesky, coupling and RHS substitutions), the
+// slice products, the separators' RHS update; then the top block and the
+// downward pass, one launch each.
+static cudaError_t run_levels_emu_small(bdss_ctx *h, const Args<double> &a, bool rhs) {
+  const Plan &p = h->plan;
+  const int cap = h->bps * h->sms;
+  Args<double> b = a;
+  if (!rhs) b.d = 0;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < p.L && e == cudaSuccess; ++l) {
+    const long long nElim = p.Nl[l] / 2;
+    kt_begin(h, h->kt_cls);
+    e = launch_phaseA<double>(b, l, 1, grid_for(h, nElim * parts_A<double>(p, l, true, cap)), h->smem, h->stream);
+    kt_end(h, 1);
+    h->launches += 1;
+    if (e == cudaSuccess) e = schur_emu_level(h, b, l);
+  }
+  kt_begin(h, h->kt_cls);
+  if (e == cudaSuccess) e = launch_top<double>(b, 1, h->smem, h->stream);
+  kt_end(h, 1);
+  h->launches += 1;
+  if (rhs)
+    for (int l = p.L - 1; l >= 0 && e == cudaSuccess; --l) {
+      kt_begin(h, h->kt_cls);
+      e = launch_phaseC<double>(b, l, grid_for(h, p.Nl[l] / 2), h->smem, h->stream);
+      kt_end(h, 1);
+      h->launches += 1;
+    }
   return e;
 }
 
@@ -437,6 +477,9 @@ template <typename T>
 static cudaError_t run_levels(bdss_ctx *h, const Args<T> &a, bool factor, bool rhs) {
   const Plan &p = h->plan;
   if (h->large) return run_levels_large<T>(h, a, factor, rhs);
+  if constexpr (sizeof(T) == 8) {
+    if (factor && h->schur_emu_on) return run_levels_emu_small(h, a, rhs);
+  }
   const int cap = h->bps * h->sms;
   if (h->persistent) {
     long long most = 1;  // tasks of the busiest step
@@ -647,7 +690,7 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
       }
     }
   }
-  if (ok && h->large && prec == BDSS_FP64 && N > 1) {  // Schur products on the tensor cores
+  if (ok && prec == BDSS_FP64 && N > 1 && (h->large || n >= 32)) {  // Schur products on the tensor cores
     ok = ws_alloc(h, (void **)&h->Wslc, emu_wslc_bytes(N - 1, n));
     ok = ok && ws_alloc(h, (void **)&h->Wexp, (size_t)(N - 1) * n * sizeof(int));
     if (ok) {
@@ -657,7 +700,10 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
         return cuda_fail(ec);
       }
       h->schur_emu_ready = 1;
-      h->schur_emu_on = 1;
+      // on by default for the tiled path; for n <= 64 the slice products do
+      // not yet beat the FP64 pipe (half of each 128-row tile is padding),
+      // so there the option opts in
+      h->schur_emu_on = h->large ? 1 : 0;
     }
   }
   if (!ok) {

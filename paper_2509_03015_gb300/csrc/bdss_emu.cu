@@ -613,6 +613,40 @@ __global__ void __launch_bounds__(256) k_emu_slice_w(long long rows, int n, int 
   }
 }
 
+// An accumulator entry: an exact integer |x| < 2^22 held in FP32.  Adding
+// 1.5 * 2^23 puts it in the binade of unit spacing, so its bits minus those
+// of 1.5 * 2^23 are x (integer pipe only).
+__device__ __forceinline__ int emu_acc_int(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+// V 2^E rounded once to FP64 (round to nearest even), built from the bits of
+// the 128-bit integer: the leading one sets the exponent, the next 52 bits the
+// fraction.  Results outside the normal range take the FP64 path.
+__device__ __forceinline__ double emu_i128_to_double(__int128 V, int E) {
+  if (V == 0) return 0.0;
+  const bool neg = V < 0;
+  unsigned __int128 m = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
+  const unsigned long long hi0 = (unsigned long long)(m >> 64), lo0 = (unsigned long long)m;
+  const int lz = hi0 ? __clzll((long long)hi0) : 64 + __clzll((long long)lo0);
+  m <<= lz;  // leading one at bit 127
+  unsigned long long top = (unsigned long long)(m >> 75);  // 53 bits
+  const unsigned __int128 rem = m & ((((unsigned __int128)1) << 75) - 1);
+  const unsigned __int128 half = ((unsigned __int128)1) << 74;
+  if (rem > half || (rem == half && (top & 1ULL))) ++top;
+  int e2 = 127 - lz + E;
+  if (top >> 53) {
+    top >>= 1;
+    ++e2;
+  }
+  const int be = e2 + 1023;
+  if (be <= 0 || be >= 2047)
+    return scalbn(ldexp((double)(long long)(V >> 64), 64) + (double)(unsigned long long)V, E);
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (top & ((1ULL << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *bar) {
   asm volatile(
@@ -648,11 +682,11 @@ __host__ __device__ inline int schur_tiles_per_sep(int n) {
 // Output tile u of the level: separator k, a D tile (lower set) or an E tile,
 // and its rounds (stored blocks of the A and B operands).
 struct SchurTile {
-  long long k, ra[kSchurRounds], rb[kSchurRounds];
+  long long k, ra0, ra1, rb0, rb1;  // stored blocks of the A and B operands of rounds 0, 1
   int isD, mt, ct, nr;
-  // operands of round r (selects, so that the tile stays in registers)
-  __device__ long long a_of(int r) const { return r == 0 ? ra[0] : ra[1]; }
-  __device__ long long b_of(int r) const { return r == 0 ? rb[0] : rb[1]; }
+  // scalar fields and selects, so that the tile stays in registers
+  __device__ long long a_of(int r) const { return r == 0 ? ra0 : ra1; }
+  __device__ long long b_of(int r) const { return r == 0 ? rb0 : rb1; }
 };
 __device__ __forceinline__ SchurTile schur_tile(long long u, long long Nl, int n) {
   SchurTile T;
@@ -665,6 +699,7 @@ __device__ __forceinline__ SchurTile schur_tile(long long u, long long Nl, int n
   T.mt = 0;
   T.ct = 0;
   T.nr = 0;
+  T.ra0 = T.ra1 = T.rb0 = T.rb1 = 0;
   for (int mt = 0; mt < MT; ++mt) {
     const int c = schur_d_cols(n, mt);
     if (r < c) {
@@ -676,22 +711,17 @@ __device__ __forceinline__ SchurTile schur_tile(long long u, long long Nl, int n
     r -= c;
   }
   if (T.isD) {
-    if (s >= 2) {
-      T.ra[T.nr] = s - 1;
-      T.rb[T.nr] = s - 1;
-      ++T.nr;
-    }
-    if (s + 1 < Nl) {
-      T.ra[T.nr] = s;
-      T.rb[T.nr] = s;
-      ++T.nr;
-    }
+    const bool hasM = s >= 2, hasP = s + 1 < Nl;
+    // round 0: the left neighbour's block if present, else the right one's
+    T.ra0 = T.rb0 = hasM ? s - 1 : s;
+    T.ra1 = T.rb1 = s;
+    T.nr = (int)hasM + (int)hasP;
   } else {
     T.mt = r / CT;
     T.ct = r - T.mt * CT;
     if (s + 2 < Nl) {
-      T.ra[0] = s + 1;
-      T.rb[0] = s;
+      T.ra0 = s + 1;
+      T.rb0 = s;
       T.nr = 1;
     }
   }
@@ -843,7 +873,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         if (lane != 0) emu_try(&acc_full, fph);
         fph ^= 1;
         tc_fence_after();
-        double v[kSchurN];
+        // the 19 diagonals, combined exactly on the integer pipe: V = sum_t
+        // ACC_t 64^(18 - t) in three int64 groups (t 0-6, 7-13, 14-18), then
+        // one 128-bit integer (|V| < 2^126: a sum of K <= 256 products of
+        // 59-bit numbers); the FP64 pipe (64 cycles per warp instruction on
+        // this GPU) is left to one add per entry
+        __int128 V[kSchurN];
         {
           long long G[kSchurN];
 #pragma unroll
@@ -853,12 +888,13 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             tmem_ld16(lane_base + (uint32_t)(t * kSchurN), rr);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < kSchurN; ++c) G[c] = G[c] * 64 + (long long)__float2int_rn(__uint_as_float(rr[c]));
+            for (int c = 0; c < kSchurN; ++c) G[c] = G[c] * 64 + (long long)emu_acc_int(rr[c]);
             if (t == 6 || t == 13 || t == kDiag - 1) {
-              const double w = t == 6 ? 4722366482869645213696.0 /* 2^72 */ : t == 13 ? 1073741824.0 /* 2^30 */ : 1.0;
+              const int sh = t == 6 ? 72 : t == 13 ? 30 : 0;
 #pragma unroll
               for (int c = 0; c < kSchurN; ++c) {
-                v[c] = (t == 6) ? (double)G[c] * w : fma((double)G[c], w, v[c]);
+                const __int128 g = (__int128)G[c] << sh;
+                V[c] = (t == 6) ? g : V[c] + g;
                 G[c] = 0;
               }
             }
@@ -874,7 +910,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
           // an Inf or NaN in either row (exponent field all ones: E = 1025)
           // poisons the entry, as an FP64 product would
           acc[c] += (Ea > 1024 || Eb > 1024) ? __longlong_as_double(0x7FF8000000000000LL)
-                                             : scalbn(v[c], Ea + Eb - 2 * kFrac);
+                                             : emu_i128_to_double(V[c], Ea + Eb - 2 * kFrac);
         }
       }
       if (stop || row >= n) continue;

@@ -157,7 +157,7 @@ def _exact_residual_is_zero(s, X, scale_bits=8):
     return True
 
 
-@pytest.mark.parametrize("n,d", [(96, 1), (200, 3), (256, 2)])
+@pytest.mark.parametrize("n,d", [(32, 2), (48, 1), (64, 4), (96, 1), (200, 3), (256, 2)])
 def test_schur_emu_exact_on_integer_couplings(n, d):
     """Both engines give the same bits, and that is the exact solution (the
     FP64 oracle, which eliminates in another order, is not exact here: the
@@ -223,7 +223,7 @@ def test_schur_emu_not_spd_reports_block():
     solver.close()
 
 
-@pytest.mark.parametrize("n,prec", [(32, "fp64"), (128, "fp32_ir")])
+@pytest.mark.parametrize("n,prec", [(16, "fp64"), (128, "fp32_ir")])
 def test_schur_emu_option_is_refused_elsewhere(n, prec):
     from paper_2509_03015_gb300 import BDSSError, Solver
     s = Solver(8, n, d_max=2, precision=prec)
@@ -232,3 +232,40 @@ def test_schur_emu_option_is_refused_elsewhere(n, prec):
     assert e.value.status == 8
     s.set_option("schur_emu", 0)
     s.close()
+
+
+# n <= 64: the per-level FP64 factorisation with the Schur products on the
+# tensor cores (default for n = 64 and N >= 1024; forced on for the others).
+@pytest.mark.parametrize("N,n,d", [(1024, 64, 4), (2000, 64, 1), (37, 64, 3), (100, 32, 2), (513, 48, 2),
+                                   (2, 64, 2)])
+def test_schur_emu_small_blocks_match_oracle(oracle_mod, N, n, d):
+    s = inputs.random_btd(N, n, d, seed=70 + N + n)
+    Xe, lde = _fp64_solve(s, schur_emu=True)
+    Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
+    assert oracle_mod.forward_error(Xe, Xo) <= 1e-10
+    assert oracle_mod.backward_error(s["A_diag"], s["A_sub"], Xe, s["B"]) <= 1e-14
+    Xa, _ = _fp64_solve(s, schur_emu=False)
+    assert oracle_mod.forward_error(Xe, Xa) <= 1e-12
+    L, _ = oracle_mod.factor(s["A_diag"], s["A_sub"])
+    ldo = oracle_mod.logdet(L)
+    assert abs(lde - ldo) <= 1e-12 * max(1.0, abs(ldo))
+
+
+def test_schur_emu_small_opt_in_and_separate_solve(oracle_mod):
+    """At the headline's block size the engine is opt-in; a factor followed
+    by a separate solve gives the fused call's result."""
+    from paper_2509_03015_gb300 import Solver
+    N, n, d = 1500, 64, 4
+    s = inputs.kalman_btd(N, n, 32, d, 0.95, 1)
+    Ad, As, B = _dev(s["A_diag"]), _dev(s["A_sub"]), _dev(s["B"])
+    sol = Solver(N, n, d_max=d)
+    assert sol.factor_solve(Ad, As, B) is not None and sol.launch_stats()[0] == 1  # persistent FP64 ALU
+    sol.set_option("schur_emu", 1)
+    X1 = sol.factor_solve(Ad, As, B).cpu().numpy()
+    assert sol.launch_stats()[0] > 1  # per-level launches, not the single persistent one
+    sol.factor(Ad, As)
+    X2 = sol.solve(B).cpu().numpy()
+    sol.close()
+    Xo = oracle_mod.solve_system(s["A_diag"], s["A_sub"], s["B"])
+    assert oracle_mod.forward_error(X1, Xo) <= 1e-10
+    assert oracle_mod.forward_error(X2, X1) <= 1e-13
