@@ -576,8 +576,66 @@ cudaError_t encode_bf16_2d(CUtensorMap *out, void *base, unsigned long long cols
 // ===========================================================================
 constexpr int kSchurN = 16;      // output columns of a tile
 constexpr int kSchurRounds = 2;  // products of one tile at most
+constexpr int kSchurAStages = 10;  // A slabs in flight (one round of ten slices)
+
+// Digit formats of the Schur engine.  Ten signed base-64 digits (59 bits)
+// for K up to 256 (the n > 64 path); eight signed base-256 digits (60 bits)
+// for K = 64 (n <= 64): |ACC_t| <= 8 x 64 x 128 x 128 = 2^23 stays exact in
+// FP32, and 15 diagonals x 16 columns leave room for two accumulators in the
+// 512 TMEM columns, so that a round's epilogue runs under the next round's
+// products.  Diagonal groups of the int64 combination: t <= kG0 (shift kSh0),
+// t <= kG1 (shift kSh1), the rest (shift 0).
+template <int kSl> struct EmuDigits;
+template <> struct EmuDigits<10> {
+  static constexpr int kBits = 6, kFrac = 59, kDg = 19, kG0 = 6, kG1 = 13, kSh0 = 72, kSh1 = 30, kBuf = 1;
+  static constexpr unsigned long long kBias = 32ULL * 18300341342965825ULL;  // 32 (64^10 - 1) / 63
+};
+template <> struct EmuDigits<8> {
+  static constexpr int kBits = 8, kFrac = 60, kDg = 15, kG0 = 4, kG1 = 9, kSh0 = 80, kSh1 = 40, kBuf = 2;
+  static constexpr unsigned long long kBias = 0x8080808080808080ULL;  // 128 (256^8 - 1) / 255
+};
+
+// q = round(v 2^(F - E)) as in emu_fixed, for the format's F.
+template <int kSl>
+__device__ __forceinline__ long long emu_fixed_t(double v, int E) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) return 0;
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int sh = ex - 1075 + EmuDigits<kSl>::kFrac - E;
+  long long q;
+  constexpr int cap = EmuDigits<kSl>::kFrac - 53;  // |v| < 2^E keeps sh <= cap
+  if (sh >= 0) q = m << (sh > cap ? cap : sh);
+  else if (sh > -63) q = (m + (1LL << (-sh - 1))) >> (-sh);
+  else q = 0;
+  return b < 0 ? -q : q;
+}
+
+// kSl digit planes of four consecutive entries (the biased digits of
+// u = q + bias, each d + B/2 with B the base, as in emu_store_quad).
+template <int kSl>
+__device__ __forceinline__ void emu_store_quad_t(const double (&v)[4], int E, unsigned short *dst,
+                                                 size_t plane_stride) {
+  constexpr int B = EmuDigits<kSl>::kBits;
+  constexpr unsigned long long mask = (1ULL << B) - 1;
+  constexpr float off = 8388608.0f + (float)(1 << (B - 1));
+  unsigned long long u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u[j] = (unsigned long long)emu_fixed_t<kSl>(v[j], E) + EmuDigits<kSl>::kBias;
+#pragma unroll
+  for (int p = 0; p < kSl; ++p) {
+    unsigned h[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int dg = p == 0 ? (int)(u[j] >> (B * (kSl - 1))) : (int)((u[j] >> (B * (kSl - 1 - p))) & mask);
+      h[j] = __float_as_uint(__int_as_float(0x4B000000 + dg) - off) >> 16;
+    }
+    *reinterpret_cast<uint2 *>(dst + (size_t)p * plane_stride) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+  }
+}
 
 // One warp per row b n + m of the level's stored blocks.
+template <int kSl>
 __global__ void __launch_bounds__(256) k_emu_slice_w(long long rows, int n, int np, const double *W,
                                                      unsigned short *Wslc, int *Wexp) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -605,11 +663,11 @@ __global__ void __launch_bounds__(256) k_emu_slice_w(long long rows, int n, int 
   }
   const int E = emu_exp(mx);
   if (lane == 0) Wexp[row] = E;
-  unsigned short *dst = Wslc + ((size_t)b * kS * n + m) * np;
+  unsigned short *dst = Wslc + ((size_t)b * kSl * n + m) * np;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int k = 4 * (lane + 32 * i);
-    if (k < np) emu_store_quad(v[i], E, dst + k, (size_t)n * np);
+    if (k < np) emu_store_quad_t<kSl>(v[i], E, dst + k, (size_t)n * np);
   }
 }
 
@@ -730,24 +788,30 @@ __device__ __forceinline__ SchurTile schur_tile(long long u, long long Nl, int n
 
 // Roles as in the residual kernel: warp 0 TMA, warp 1 MMA, warps 2-5 the
 // epilogue of one TMEM lane quarter each.  Every wait is bounded.
+template <int kSl>
 __global__ void __launch_bounds__(kEmuThreads, 1)
     k_emu_schur(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const __grid_constant__ EmuSchurArgs a) {
+  using Fm = EmuDigits<kSl>;
+  constexpr int kNs = kSl * kSchurN;           // B rows: the kSl slices of 16 columns stacked (MMA N)
+  constexpr int kBTile = kNs * kEmuKc * 2;     // bytes of one B stage
+  constexpr int kAccCols = Fm::kDg * kSchurN;  // TMEM columns of one accumulator
+  constexpr int kNB = Fm::kBuf;                // accumulators (rounds in flight)
+  constexpr int kAS = kSchurAStages;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint64_t a_full[kAStages], a_empty[kAStages], b_full[kXStages], b_empty[kXStages];
-  __shared__ uint64_t acc_full, acc_empty, drain;
+  __shared__ uint64_t a_full[kAS], a_empty[kAS], b_full[kXStages], b_empty[kXStages];
+  __shared__ uint64_t acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                          ~(uintptr_t)1023);
-  unsigned char *Ast = base;                              // kAStages x 16 KB
-  unsigned char *Bst = base + (size_t)kAStages * kATile;  // kXStages x 20 KB
+  unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char *Ast = base;                         // kAS x 16 KB
+  unsigned char *Bst = base + (size_t)kAS * kATile;  // kXStages x kBTile
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, kchunks = a.np / kEmuKc;
   const long long tiles = ((a.Nl + 1) / 2) * schur_tiles_per_sep(n);
   volatile int *abort = &s_abort;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kAStages; ++s) {
+    for (int s = 0; s < kAS; ++s) {
       mbar_init(&a_full[s], 1);
       mbar_init(&a_empty[s], 1);
     }
@@ -755,8 +819,10 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
     mbar_init(&drain, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -781,21 +847,21 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         for (int r = 0; r < T.nr && !*abort; ++r)
           for (int kk = 0; kk < kchunks; ++kk) {
             if (!emu_wait(&b_empty[bs], bph ^ 1, a.timeout_ns, abort)) { fail(); break; }
-            mbar_expect_tx(&b_full[bs], kXTile);
-            tma_load_3d(Bst + (size_t)bs * kXTile, &mapB, kk * kEmuKc, T.ct * kSchurN, (int)(T.b_of(r) * kS),
+            mbar_expect_tx(&b_full[bs], kBTile);
+            tma_load_3d(Bst + (size_t)bs * kBTile, &mapB, kk * kEmuKc, T.ct * kSchurN, (int)(T.b_of(r) * kSl),
                         &b_full[bs]);
             if (++bs == kXStages) { bs = 0; bph ^= 1; }
-            for (int p = 0; p < kS; ++p) {
+            for (int p = 0; p < kSl; ++p) {
               if (!emu_wait(&a_empty[as], aph ^ 1, a.timeout_ns, abort)) { fail(); break; }
               mbar_expect_tx(&a_full[as], kATile);
-              tma_load_2d(Ast + (size_t)as * kATile, &mapA, kk * kEmuKc, (int)((T.a_of(r) * kS + p) * n + T.mt * kM),
+              tma_load_2d(Ast + (size_t)as * kATile, &mapA, kk * kEmuKc, (int)((T.a_of(r) * kSl + p) * n + T.mt * kM),
                           &a_full[as]);
-              if (++as == kAStages) { as = 0; aph ^= 1; }
+              if (++as == kAS) { as = 0; aph ^= 1; }
             }
             if (*abort) break;
           }
       }
-      for (int s = 0; s < kAStages; ++s) {
+      for (int s = 0; s < kAS; ++s) {
         const uint32_t ph = (s < as) ? aph : (aph ^ 1);
         emu_wait(&a_full[s], ph, a.timeout_ns, nullptr);
       }
@@ -807,34 +873,37 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
   } else if (warp == 1) {
     // ---- MMA issuer ------------------------------------------------------------
     if (lane == 0) {
-      constexpr uint32_t idesc = emu_idesc(kM, kN);
+      constexpr uint32_t idesc = emu_idesc(kM, kNs);
       int as = 0, bs = 0;
-      uint32_t aph = 0, bph = 0, eph = 0;
+      uint32_t aph = 0, bph = 0;
+      long long i = 0;  // rounds so far: accumulator i % kNB
       for (long long u = blockIdx.x; u < tiles && !*abort; u += gridDim.x) {
         const SchurTile T = schur_tile(u, a.Nl, n);
         for (int r = 0; r < T.nr && !*abort; ++r) {
-          if (!emu_wait(&acc_empty, eph, a.timeout_ns, abort)) { fail(); break; }
-          eph ^= 1;
+          const int ab = (int)(i % kNB);
+          if (!emu_wait(&acc_empty[ab], (uint32_t)((i / kNB) & 1), a.timeout_ns, abort)) { fail(); break; }
           tc_fence_after();
+          const uint32_t dacc = tmem + (uint32_t)(ab * kAccCols);
           for (int kk = 0; kk < kchunks; ++kk) {
             if (!emu_wait(&b_full[bs], bph, a.timeout_ns, abort)) { fail(); break; }
-            const unsigned char *bb = Bst + (size_t)bs * kXTile;
-            for (int p = 0; p < kS; ++p) {
+            const unsigned char *bb = Bst + (size_t)bs * kBTile;
+            for (int p = 0; p < kSl; ++p) {
               if (!emu_wait(&a_full[as], aph, a.timeout_ns, abort)) { fail(); break; }
               tc_fence_after();
-              const unsigned char *ab = Ast + (size_t)as * kATile;
+              const unsigned char *abuf = Ast + (size_t)as * kATile;
 #pragma unroll
               for (int ks = 0; ks < kEmuKc / 16; ++ks)
-                emu_mma_bf16(tmem + (uint32_t)(p * kSchurN), tc_desc_sw128(ab, ks * 32), tc_desc_sw128(bb, ks * 32),
+                emu_mma_bf16(dacc + (uint32_t)(p * kSchurN), tc_desc_sw128(abuf, ks * 32), tc_desc_sw128(bb, ks * 32),
                              idesc);
               tc_commit(&a_empty[as]);
-              if (++as == kAStages) { as = 0; aph ^= 1; }
+              if (++as == kAS) { as = 0; aph ^= 1; }
             }
             tc_commit(&b_empty[bs]);
             if (++bs == kXStages) { bs = 0; bph ^= 1; }
             if (*abort) break;
           }
-          tc_commit(&acc_full);
+          tc_commit(&acc_full[ab]);
+          ++i;
         }
       }
       tc_commit(&drain);
@@ -844,14 +913,14 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
     // ---- epilogue: warps 2..5, TMEM lane quarter warp % 4 ---------------------
     const int quarter = warp & 3;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
-    auto clear = [&]() {
-      for (int t = 0; t < kDiag; ++t) tmem_zero16(lane_base + (uint32_t)(t * kSchurN));
+    auto clear = [&](int b) {
+      for (int t = 0; t < Fm::kDg; ++t) tmem_zero16(lane_base + (uint32_t)(b * kAccCols + t * kSchurN));
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       tc_fence_before();
-      emu_arrive(&acc_empty);
+      emu_arrive(&acc_empty[b]);
     };
-    clear();
-    uint32_t fph = 0;
+    for (int b = 0; b < kNB; ++b) clear(b);
+    long long i = 0;  // rounds so far: accumulator i % kNB
     const size_t nn = (size_t)n * n;
     bool stop = false;
     for (long long u = blockIdx.x; u < tiles && !stop; u += gridDim.x) {
@@ -862,46 +931,52 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 #pragma unroll
       for (int c = 0; c < kSchurN; ++c) acc[c] = 0.0;
       for (int r = 0; r < T.nr; ++r) {
+        const int ab = (int)(i % kNB);
+        const uint32_t fpar = (uint32_t)((i / kNB) & 1);
         int ok = 0;
-        if (lane == 0) ok = emu_wait(&acc_full, fph, a.timeout_ns, abort) ? 1 : 0;
+        if (lane == 0) ok = emu_wait(&acc_full[ab], fpar, a.timeout_ns, abort) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) fail();
           stop = true;
           break;
         }
-        if (lane != 0) emu_try(&acc_full, fph);
-        fph ^= 1;
+        if (lane != 0) emu_try(&acc_full[ab], fpar);
+        ++i;
         tc_fence_after();
-        // the 19 diagonals, combined exactly on the integer pipe: V = sum_t
-        // ACC_t 64^(18 - t) in three int64 groups (t 0-6, 7-13, 14-18), then
-        // one 128-bit integer (|V| < 2^126: a sum of K <= 256 products of
-        // 59-bit numbers); the FP64 pipe (64 cycles per warp instruction on
-        // this GPU) is left to one add per entry
+        // the diagonals, combined exactly on the integer pipe: V = sum_t
+        // ACC_t B^(kDg - 1 - t) in three int64 groups, then one 128-bit
+        // integer (|V| < 2^126: a sum of K products of F-bit numbers, K <= 256
+        // for F = 59, K = 64 for F = 60); the FP64 pipe (64 cycles per warp
+        // instruction on this GPU) is left to one add per entry
         __int128 V[kSchurN];
         {
           long long G[kSchurN];
 #pragma unroll
           for (int c = 0; c < kSchurN; ++c) G[c] = 0;
-          for (int t = 0; t < kDiag; ++t) {
+          for (int t = 0; t < Fm::kDg; ++t) {
             uint32_t rr[16];
-            tmem_ld16(lane_base + (uint32_t)(t * kSchurN), rr);
+            tmem_ld16(lane_base + (uint32_t)(ab * kAccCols + t * kSchurN), rr);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < kSchurN; ++c) G[c] = G[c] * 64 + (long long)emu_acc_int(rr[c]);
-            if (t == 6 || t == 13 || t == kDiag - 1) {
-              const int sh = t == 6 ? 72 : t == 13 ? 30 : 0;
+            for (int c = 0; c < kSchurN; ++c) {
+              // |ACC| < 2^22 (ten digits) takes the integer trick; up to 2^23 a conversion
+              const int x = (kSl == 10) ? emu_acc_int(rr[c]) : __float2int_rn(__uint_as_float(rr[c]));
+              G[c] = G[c] * (1LL << Fm::kBits) + (long long)x;
+            }
+            if (t == Fm::kG0 || t == Fm::kG1 || t == Fm::kDg - 1) {
+              const int sh = t == Fm::kG0 ? Fm::kSh0 : t == Fm::kG1 ? Fm::kSh1 : 0;
 #pragma unroll
               for (int c = 0; c < kSchurN; ++c) {
                 const __int128 g = (__int128)G[c] << sh;
-                V[c] = (t == 6) ? g : V[c] + g;
+                V[c] = (t == Fm::kG0) ? g : V[c] + g;
                 G[c] = 0;
               }
             }
           }
         }
         tc_fence_before();
-        clear();
+        clear(ab);
         const int Ea = row < n ? __ldg(a.Wexp + (size_t)T.a_of(r) * n + row) : 0;
 #pragma unroll
         for (int c = 0; c < kSchurN; ++c) {
@@ -910,7 +985,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
           // an Inf or NaN in either row (exponent field all ones: E = 1025)
           // poisons the entry, as an FP64 product would
           acc[c] += (Ea > 1024 || Eb > 1024) ? __longlong_as_double(0x7FF8000000000000LL)
-                                             : emu_i128_to_double(V[c], Ea + Eb - 2 * kFrac);
+                                             : emu_i128_to_double(V[c], Ea + Eb - 2 * Fm::kFrac);
         }
       }
       if (stop || row >= n) continue;
@@ -979,7 +1054,8 @@ cudaError_t emu_configure() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const void *kernels[] = {(const void *)k_emu_residual, (const void *)k_emu_slice_operator,
-                           (const void *)k_emu_slice_x, (const void *)k_emu_schur};
+                           (const void *)k_emu_slice_x, (const void *)k_emu_schur<10>,
+                           (const void *)k_emu_schur<8>};
   for (const void *k : kernels) {
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
@@ -1032,27 +1108,38 @@ cudaError_t launch_emu_residual(long long N, int n, int d, const double *X, cons
 
 size_t emu_wslc_bytes(long long nW, int n) { return (size_t)nW * kS * n * emu_np(n) * 2; }
 
+// Digits of the Schur engine: eight base-256 digits when the whole K = n fits
+// one chunk of 64 (two accumulators in TMEM), else ten base-64 digits.
+static int schur_slices(int n) { return emu_np(n) == kEmuKc ? 8 : 10; }
+
+template <int kSl>
+static size_t schur_smem() {
+  return (size_t)kSchurAStages * kATile + (size_t)kXStages * kSl * kSchurN * kEmuKc * 2 + 1024;
+}
+
 cudaError_t launch_emu_slice_w(long long nW, int n, const double *W, unsigned short *Wslc, int *Wexp,
                                cudaStream_t s) {
   if (n > 256) return cudaErrorInvalidValue;
   const long long rows = nW * n;
   if (rows <= 0) return cudaSuccess;
-  k_emu_slice_w<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(rows, n, emu_np(n), W, Wslc, Wexp);
+  const unsigned grid = (unsigned)((rows + 7) / 8);
+  if (schur_slices(n) == 8) k_emu_slice_w<8><<<grid, 256, 0, s>>>(rows, n, emu_np(n), W, Wslc, Wexp);
+  else k_emu_slice_w<10><<<grid, 256, 0, s>>>(rows, n, emu_np(n), W, Wslc, Wexp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emu_schur(long long Nl, int n, int l, const unsigned short *Wslc, const int *Wexp,
-                             const double *A_diag, double *Ld, double *En, DevStatus *st, long long timeout_ns,
-                             int sms, cudaStream_t s) {
-  if (Nl < 2 || n > 256) return cudaErrorInvalidValue;
+template <int kSl>
+static cudaError_t launch_emu_schur_t(long long Nl, int n, int l, const unsigned short *Wslc, const int *Wexp,
+                                      const double *A_diag, double *Ld, double *En, DevStatus *st,
+                                      long long timeout_ns, int sms, cudaStream_t s) {
   const int np = emu_np(n);
   const long long nW = Nl - 1;
   CUtensorMap mapA, mapB;
-  cudaError_t e = encode_bf16_2d(&mapA, (void *)Wslc, (unsigned long long)np, (unsigned long long)(nW * kS * n),
+  cudaError_t e = encode_bf16_2d(&mapA, (void *)Wslc, (unsigned long long)np, (unsigned long long)(nW * kSl * n),
                                  kEmuKc, kM);
   if (e == cudaSuccess)
     e = encode_bf16_3d(&mapB, (void *)Wslc, (unsigned long long)np, (unsigned long long)n,
-                       (unsigned long long)(nW * kS), kEmuKc, kSchurN, kS);
+                       (unsigned long long)(nW * kSl), kEmuKc, kSchurN, kSl);
   if (e != cudaSuccess) return e;
   EmuSchurArgs k;
   k.Nl = Nl;
@@ -1067,8 +1154,17 @@ cudaError_t launch_emu_schur(long long Nl, int n, int l, const unsigned short *W
   k.timeout_ns = timeout_ns;
   const long long tiles = ((Nl + 1) / 2) * schur_tiles_per_sep(n);
   const int grid = (int)(tiles < sms ? tiles : sms);
-  k_emu_schur<<<grid, kEmuThreads, kResidualSmem, s>>>(mapA, mapB, k);
+  k_emu_schur<kSl><<<grid, kEmuThreads, schur_smem<kSl>(), s>>>(mapA, mapB, k);
   return cudaGetLastError();
+}
+
+cudaError_t launch_emu_schur(long long Nl, int n, int l, const unsigned short *Wslc, const int *Wexp,
+                             const double *A_diag, double *Ld, double *En, DevStatus *st, long long timeout_ns,
+                             int sms, cudaStream_t s) {
+  if (Nl < 2 || n > 256) return cudaErrorInvalidValue;
+  if (schur_slices(n) == 8)
+    return launch_emu_schur_t<8>(Nl, n, l, Wslc, Wexp, A_diag, Ld, En, st, timeout_ns, sms, s);
+  return launch_emu_schur_t<10>(Nl, n, l, Wslc, Wexp, A_diag, Ld, En, st, timeout_ns, sms, s);
 }
 
 }  // namespace bdss
