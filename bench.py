@@ -366,9 +366,16 @@ def other_workloads(dev, stream, world, max_over_ranks, args, oracle_job=None):
     nstar, nstar_ms = sol.tune_nstar(Ad, As, B, reps=10)
     sol.factor_solve(Ad, As, B, X)
     ms = _timed(lambda: sol.factor_solve(Ad, As, B, X), 20, stream, max_over_ranks)
+    launches, grid_barriers = sol.launch_stats()
+    path = "one-cluster" if grid_barriers == 0 else "persistent grid"
+    # the persistent grid kernel on the same system, for comparison
+    sol.set_option("small_cluster", 0)
+    sol.factor_solve(Ad, As, B, X)
+    ms_grid = _timed(lambda: sol.factor_solve(Ad, As, B, X), 20, stream, max_over_ranks)
+    sol.set_option("small_cluster", -1)
     res[name] = {"value": world * 1e3 / ms, "unit": "systems/s", "ms_per_step": ms, "nstar": nstar,
-                 "nstar_candidates_ms": nstar_ms,
-                 "note": "one call = one persistent launch + status read-back"}
+                 "nstar_candidates_ms": nstar_ms, "path": path, "persistent_grid_ms": ms_grid,
+                 "note": "one call (launch + stream synchronisation) through the C ABI, inputs on the device"}
     sol.close()
     # -- mixed precision at n = 256 --------------------------------------------
     name = "kalman-N4096-n256-d16-rho0.99"

@@ -148,6 +148,20 @@ typedef enum {
                                    (BF16 digit slices, exact FP32 accumulation: see
                                    bdss_residual); 0 = on the FP64 ALU.  Setting 1 on a
                                    handle without it gives BDSS_ERR_UNSUPPORTED */
+  BDSS_OPT_SMALL_CLUSTER = 14,  /* FP64 handles with n <= 32 and d_max <= 16: the one-cluster
+                                   path, which runs the whole factor and/or solve (the same
+                                   recursion of Sec. 3, Algorithms 4 and 7, with the same
+                                   arithmetic and factor storage as the persistent kernel) in
+                                   one launch of a single thread-block cluster (up to 16 CTAs)
+                                   with hardware cluster barriers between the phases instead
+                                   of grid-wide barriers, and writes its status into page-locked
+                                   memory itself (no status memset or copy).  -1 (default):
+                                   used with BDSS_OPT_PERSISTENT = 1 when n <= 16 and
+                                   N <= 8 x the cluster's CTAs; 1: whenever the handle has it;
+                                   0: never.  Setting 1 on a handle without it (another
+                                   precision or size, or no cluster launch on the device)
+                                   gives BDSS_ERR_UNSUPPORTED.  Its launches record no grid
+                                   barriers and no trace */
   BDSS_OPT_KERNEL_TIMING = 9    /* 1: time every launch (group) of each following call with
                                    CUDA events recorded on the handle's stream, by kernel
                                    class (bdss_kernel_class); read with

@@ -19,7 +19,7 @@ PRECISIONS = {"fp64": 0, "fp32_ir": 1, "tf32_ir": 2}
 OPTIONS = {"timeout_ms": 0, "persistent": 1, "max_refine": 2, "target_berr_e18": 3, "debug_skip_arrive": 4,
            "debug_guards": 5, "debug_corrupt_guard": 6, "refine_krylov": 7, "max_krylov_iters": 8,
            "kernel_timing": 9, "residual_emu": 10, "shift": 11, "nstar": 12,
-           "schur_emu": 13}
+           "schur_emu": 13, "small_cluster": 14}
 KERNEL_CLASSES = ("factor", "schur_tc", "solve", "correction", "residual", "krylov", "slice")
 
 

@@ -91,6 +91,11 @@ struct bdss_ctx {
   int ts_ok = 0;
   bool emu_sliced = false;
   int skip_barrier = 0;
+  // one-cluster path for short systems (FP64, n <= 32, d_max <= 16)
+  int small_opt = -1;            // -1: by size, 0: off, 1: whenever available
+  int small_cluster = 0;         // CTAs of its cluster (0: unavailable)
+  size_t small_smem = 0;         // its shared memory per CTA
+  DevStatus *hst_dev = nullptr;  // device-visible address of hst
   // stats of the last call
   int64_t launches = 0;
   int64_t barriers = 0;
@@ -256,6 +261,50 @@ static bdss_status finish(bdss_ctx *h, bdss_info *info) {
 
 static cudaError_t reset_status(bdss_ctx *h) {
   return cudaMemsetAsync(h->dst, 0, sizeof(DevStatus), h->stream);
+}
+
+// The one-cluster path: on request, or by size for systems whose level 0
+// spreads over the cluster at no more than kSmallAutoPerCta blocks per CTA
+// with n <= kSmallAutoMaxN (above that the persistent grid's SMs win).  It
+// runs in place of the persistent launch only (not with per-level launches,
+// the slice products or the barrier test hook).
+constexpr int kSmallAutoMaxN = 16;
+constexpr int kSmallAutoPerCta = 8;
+static bool use_small(const bdss_ctx *h) {
+  if (is_mixed(h) || h->small_cluster < 2 || !h->persistent || h->skip_barrier || h->schur_emu_on) return false;
+  if (h->small_opt >= 0) return h->small_opt == 1;
+  return h->n <= kSmallAutoMaxN && h->N <= (int64_t)kSmallAutoPerCta * h->small_cluster;
+}
+
+static cudaError_t run_small(bdss_ctx *h, const Args<double> &a, bool factor, bool rhs) {
+  h->launches += 1;
+  kt_begin(h, h->kt_cls);
+  const cudaError_t e =
+      launch_small(a, factor ? 1 : 0, rhs ? 1 : 0, h->small_cluster, h->small_smem, h->hst_dev, h->stream);
+  kt_end(h, 1);
+  return e;
+}
+
+// Outcome of a one-cluster launch, which cleared the device status itself
+// and wrote status, level, block and its barrier stamps into hst at its end.
+static bdss_status finish_small(bdss_ctx *h, bdss_info *info) {
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  kt_harvest(h);
+  const volatile DevStatus *hs = h->hst;
+  int c = 0;
+  while (c < kTraceSlots && hs->trace[c] != 0) {
+    h->trace[c] = hs->trace[c];
+    ++c;
+  }
+  h->trace_count = c;
+  const int st = hs->status;
+  if (info && st == BDSS_ERR_NOT_SPD) {
+    info->level = hs->level;
+    info->block = hs->block;
+  }
+  if (h->debug_guards && !guards_intact(h)) return BDSS_ERR_GUARD;
+  return (bdss_status)st;
 }
 
 template <typename T>
@@ -712,6 +761,19 @@ bdss_status bdss_create(bdss_handle *out, int64_t N, int32_t n, int32_t d_max, b
     return BDSS_ERR_ALLOC;
   }
   memset(h->hst, 0, sizeof(DevStatus));
+  if (prec == BDSS_FP64 && !h->large && n <= kSmallMaxN && d_max <= kSmallMaxD) {
+    // the one-cluster path writes its outcome straight into hst
+    void *dp = nullptr;
+    int c = 0;
+    const size_t sm = small_smem_bytes(n, d_max);
+    if (cudaHostGetDevicePointer(&dp, h->hst, 0) == cudaSuccess && dp &&
+        small_cluster_size(sm, &c) == cudaSuccess && c >= 2) {
+      h->small_cluster = c;
+      h->small_smem = sm;
+      h->hst_dev = (DevStatus *)dp;
+    }
+    cudaGetLastError();  // the path is optional: no error of the call
+  }
   *out = h;
   return BDSS_OK;
 }
@@ -761,6 +823,11 @@ bdss_status bdss_set_option(bdss_handle h, bdss_option key, int64_t value) {
       h->factored = false;
       return BDSS_OK;
     }
+    case BDSS_OPT_SMALL_CLUSTER:
+      if (value < -1 || value > 1) return BDSS_ERR_INVALID_ARG;
+      if (value == 1 && h->small_cluster < 2) return BDSS_ERR_UNSUPPORTED;
+      h->small_opt = (int)value;
+      return BDSS_OK;
     case BDSS_OPT_SHIFT:
       if (value != 0 && value != 1) return BDSS_ERR_INVALID_ARG;
       h->shift_on = (int)value;
@@ -872,7 +939,8 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
   kt_reset(h);
   h->kt_cls = BDSS_KT_FACTOR;
   const bool rhs = (B != nullptr);
-  cudaError_t e = reset_status(h);
+  const bool small = use_small(h);
+  cudaError_t e = small ? cudaSuccess : reset_status(h);
   if (e != cudaSuccess) return cuda_fail(e);
   if (!is_mixed(h)) {
     Args<double> a = base_args<double>(h);
@@ -883,7 +951,7 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
       a.B64 = B;
       a.Y = X;
     }
-    e = run_levels<double>(h, a, true, rhs);
+    e = small ? run_small(h, a, true, rhs) : run_levels<double>(h, a, true, rhs);
   } else {
     Args<float> a = base_args<float>(h);
     a.A_diag = A_diag;
@@ -898,7 +966,7 @@ static bdss_status factor_impl(bdss_ctx *h, const double *A_diag, const double *
     e = run_levels<float>(h, a, true, rhs);
   }
   if (e != cudaSuccess) return cuda_fail(e);
-  bdss_status st = finish(h, info);
+  bdss_status st = small ? finish_small(h, info) : finish(h, info);
   h->shift_used = 0.0;
   if (st == BDSS_ERR_NOT_SPD && is_mixed(h) && h->shift_on) {
     // kappa(A) u_32 near or above one: an FP32 pivot failed.  Factor
@@ -1166,16 +1234,17 @@ bdss_status bdss_solve(bdss_handle h, const double *B, double *X, int32_t d, bds
   h->barriers = 0;
   kt_reset(h);
   h->kt_cls = BDSS_KT_SOLVE;
-  cudaError_t e = reset_status(h);
+  const bool small = use_small(h);
+  cudaError_t e = small ? cudaSuccess : reset_status(h);
   if (e != cudaSuccess) return cuda_fail(e);
   if (!is_mixed(h)) {
     Args<double> a = base_args<double>(h);
     a.d = d;
     a.B64 = B;
     a.Y = X;
-    e = run_levels<double>(h, a, false, true);
+    e = small ? run_small(h, a, false, true) : run_levels<double>(h, a, false, true);
     if (e != cudaSuccess) return cuda_fail(e);
-    return finish(h, info);
+    return small ? finish_small(h, info) : finish(h, info);
   }
   if (X == B) return BDSS_ERR_INVALID_ARG;  // the residual needs B after X is written
   Args<float> a = base_args<float>(h);

@@ -229,9 +229,10 @@ class Solver:
         return L
 
     def trace(self):
-        """Grid-barrier release times (ns, device clock) of the last
-        persistent pass: start-up, then phase A / phase B of each level, then
-        one per downward level."""
+        """Barrier release times (ns, device clock) of the last persistent
+        pass: start-up, then phase A / phase B of each level, then one per
+        downward level (grid barriers; on the one-cluster path its cluster
+        barriers, with one more stamp at the end)."""
         buf = (ctypes.c_int64 * 256)()
         cnt = ctypes.c_int32()
         _lib.check(self.lib.bdss_last_trace(self.h, buf, 256, ctypes.byref(cnt)), "bdss_last_trace")
