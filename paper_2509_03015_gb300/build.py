@@ -18,7 +18,8 @@ BUILD_DIR = os.path.join(PKG, "_build")
 
 SOURCES = ["bdss_kernels.cu", "bdss_large.cu", "bdss_api.cu", "bdss_batched.cu", "bdss_noalloc.cu", "bdss_kalman.cu", "bdss_krylov.cu", "bdss_emu.cu", "bdss_chunk.cu",
            "bdss_small.cu"]
-HEADERS = ["bdss_device.cuh", "bdss_large.cuh", "bdss_tc.cuh", "bdss_launch.h", "bdss_kalman.h", "bdss_krylov.h", "bdss_emu.h", "bdss_chunk.h"]
+HEADERS = ["bdss_device.cuh", "bdss_large.cuh", "bdss_tc.cuh", "bdss_launch.h", "bdss_kalman.h", "bdss_krylov.h", "bdss_emu.h", "bdss_chunk.h",
+           "bdss_small.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", os.path.join(ROOT, "include")]

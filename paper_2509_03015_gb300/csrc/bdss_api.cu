@@ -18,6 +18,7 @@
 #include "bdss_launch.h"
 #include "bdss_kalman.h"
 #include "bdss_krylov.h"
+#include "bdss_small.h"
 
 using namespace bdss;
 

@@ -27,19 +27,6 @@ cudaError_t launch_logdet(long long N, int n, int Ltop_level, const T *Ld, const
                           cudaStream_t s);
 cudaError_t launch_residual(long long N, int n, int d, const double *A_diag, const double *A_sub, const double *X,
                             const double *B, float *R32, DevStatus *st, int with_norm, int grid, cudaStream_t s);
-// One-cluster path for short systems of small blocks (bdss_small.cu): FP64,
-// n <= kSmallMaxN, d <= kSmallMaxD, the whole call in one launch of a single
-// thread-block cluster of up to 16 CTAs with cluster barriers between the
-// phases.  small_cluster_size finds the largest supported cluster (16, 8, 4
-// or 2 CTAs; 0: none) for `smem` bytes per CTA; `out` is a device-visible
-// address of the page-locked status copy the kernel writes at its end.
-constexpr int kSmallThreads = 128;
-constexpr int kSmallMaxN = 32;
-constexpr int kSmallMaxD = 16;
-size_t small_smem_bytes(int n, int d);
-cudaError_t small_cluster_size(size_t smem, int *cluster);
-cudaError_t launch_small(const Args<double> &a, int factor, int rhs, int cluster, size_t smem, DevStatus *out,
-                         cudaStream_t s);
 cudaError_t launch_adjoint_grads(long long N, int n, int d, const double *Lam, const double *X, double *dA_diag,
                                  double *dA_sub, int grid, cudaStream_t s);
 

@@ -26,6 +26,7 @@
 
 #include "bdss_device.cuh"
 #include "bdss_launch.h"
+#include "bdss_small.h"
 
 namespace cg = cooperative_groups;
 
