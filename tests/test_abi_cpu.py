@@ -109,3 +109,21 @@ def test_binding_rejects_pageable_host_tensors():
         _check_tensor(t, "X", (2, 3, 3))
     with pytest.raises(ValueError):
         _check_tensor(t.float(), "A_diag", (2, 3, 3), host_ok=True)
+
+
+def _enum_values(name):
+    """Members and values of the C enum `name` in include/bdss.h."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef enum \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    return {k: int(v) for k, v in re.findall(r"\b([A-Z][A-Z0-9_]+)\s*=\s*(\d+)", body)}
+
+
+def test_binding_option_table_matches_the_header():
+    """Every bdss_option the header declares has the same number in the
+    binding's option table, and the table names no other number."""
+    from paper_2509_03015_gb300 import _lib
+    opts = _enum_values("bdss_option")
+    assert opts["BDSS_OPT_SMALL_CLUSTER"] == 14
+    assert sorted(_lib.OPTIONS.values()) == sorted(opts.values())
+    for key, value in _lib.OPTIONS.items():
+        assert opts["BDSS_OPT_" + key.upper()] == value, key
