@@ -79,8 +79,9 @@ def fp32_peak(sms, mhz):
 
 
 def measured_peaks():
-    """HBM GB/s and dense BF16 TFLOP/s measured on the GB300s (file
-    written by the driver), else the earlier measurement's figures."""
+    """HBM GB/s and dense BF16 TFLOP/s measured on these GB300s (a copy and a
+    cuBLAS BF16 GEMM, in MEASURED_PEAKS.json), else an earlier measurement's
+    figures."""
     try:
         with open(PEAKS) as f:
             p = json.load(f)
