@@ -156,8 +156,10 @@ typedef enum {
                                    with hardware cluster barriers between the phases instead
                                    of grid-wide barriers, and writes its status into page-locked
                                    memory itself (no status memset or copy).  -1 (default):
-                                   used with BDSS_OPT_PERSISTENT = 1 when n <= 16 and
-                                   N <= 8 x the cluster's CTAs; 1: whenever the handle has it;
+                                   used with BDSS_OPT_PERSISTENT = 1 when n <= 16,
+                                   N <= 8 x the cluster's CTAs and N n <= 64 x the
+                                   cluster's CTAs (where it measured faster than the
+                                   grid kernel); 1: whenever the handle has it;
                                    0: never.  Setting 1 on a handle without it (another
                                    precision or size, or no cluster launch on the device)
                                    gives BDSS_ERR_UNSUPPORTED.  Its launches record no grid

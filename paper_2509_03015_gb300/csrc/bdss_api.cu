@@ -264,17 +264,22 @@ static cudaError_t reset_status(bdss_ctx *h) {
   return cudaMemsetAsync(h->dst, 0, sizeof(DevStatus), h->stream);
 }
 
-// The one-cluster path: on request, or by size for systems whose level 0
-// spreads over the cluster at no more than kSmallAutoPerCta blocks per CTA
-// with n <= kSmallAutoMaxN (above that the persistent grid's SMs win).  It
-// runs in place of the persistent launch only (not with per-level launches,
-// the slice products or the barrier test hook).
+// The one-cluster path: on request, or by size.  Its time grows with the
+// blocks each CTA eliminates in turn at level 0 and with each block's pivot
+// chain (n columns), while the persistent grid spreads level 0 over every SM:
+// measured on GB300 (d = 1) the cluster is faster up to N = 128 at n = 4 and
+// 8, N = 64 at n = 12, N = 32-64 at n = 16, and never from n = 24.  The rule
+// n <= 16, N <= 8 C and N n <= 64 C (C = the cluster's CTAs) keeps it to
+// that range.  It runs in place of the persistent launch only (not with
+// per-level launches, the slice products or the barrier test hook).
 constexpr int kSmallAutoMaxN = 16;
 constexpr int kSmallAutoPerCta = 8;
+constexpr int kSmallAutoWorkPerCta = 64;
 static bool use_small(const bdss_ctx *h) {
   if (is_mixed(h) || h->small_cluster < 2 || !h->persistent || h->skip_barrier || h->schur_emu_on) return false;
   if (h->small_opt >= 0) return h->small_opt == 1;
-  return h->n <= kSmallAutoMaxN && h->N <= (int64_t)kSmallAutoPerCta * h->small_cluster;
+  const int64_t C = h->small_cluster;
+  return h->n <= kSmallAutoMaxN && h->N <= kSmallAutoPerCta * C && h->N * h->n <= kSmallAutoWorkPerCta * C;
 }
 
 static cudaError_t run_small(bdss_ctx *h, const Args<double> &a, bool factor, bool rhs) {
