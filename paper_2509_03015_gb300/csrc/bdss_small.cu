@@ -50,7 +50,7 @@ __device__ __forceinline__ int round32(int x) { return (x + 31) & ~31; }
 
 // Staging in one round.  A phase's operands come from several blocks in L2
 // (or in page-locked host memory at level 0); staging them block by block
-// costs one dependent round trip each, which at n = 8 is most of a phase.
+// costs one dependent round trip each (about half a microsecond in L2).
 // A StageList names up to kMaxSegs row-major rows x cols sources and their
 // shared-memory destinations (stride ld; as rows, or transposed so that the
 // columns become rows), and stage_round has every thread issue the loads of
